@@ -1,0 +1,233 @@
+"""Pins of the oracle's walk, estimator and statistics (CPU only).
+
+Each test compares against something the mathematics fixes:
+
+* harmonic Dirichlet data with rho = 0 and no clipping: g(X_n) is a
+  martingale of the Gaussian walk for harmonic polynomials of degree <= 3, so
+  by optional stopping the estimator is exactly unbiased for every dt, and
+  the common-random-number difference is unbiased for the exact centred
+  difference of g;
+* constant density with g = (2 pi / 3) G rho0 |x|^2 and no clipping:
+  |X_n|^2 - 3 n sigma^2 dt is a martingale and the trapezoid sum is exactly
+  n dt rho0, so E[u] = g(x0) exactly (the quadratic solution of
+  Delta Phi = 4 pi G rho0);
+* Brownian scaling: a box scaled by R with dt scaled by R^2 replays the same
+  normalised walk, so every per-path source integral scales by R^2 (the
+  paper's E[tau] ~ R^2, Sec. 3);
+* the slab exit time E[tau] = (a - z)(a + z) with the discrete-monitoring
+  overshoot correction a -> a + 0.5826 sigma sqrt(dt) (Siegmund 1979;
+  Broadie, Glasserman & Kou 1997);
+* a brute-force restatement in pure Python on a tiny case, per path;
+* the two-pass statistics against numpy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_07469_gb300 import workloads as W
+from tests.helpers import oracle_spec
+
+HARMONIC = {
+    "linear": (0.3, 1.0, 2.0, -1.0, 0, 0, 0, 0, 0, 0, 0),
+    "x2-y2": (0, 0, 0, 0, 1.0, -1.0, 0, 0, 0, 0, 0),
+    "xyz": (0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3.0),
+    "x2+y2-2z2": (0, 0, 0, 0, 1.0, 1.0, -2.0, 0, 0, 0, 0),
+}
+
+
+def poly_eval(c, x):
+    X, Y, Z = x
+    return (c[0] + c[1] * X + c[2] * Y + c[3] * Z + c[4] * X * X + c[5] * Y * Y + c[6] * Z * Z
+            + c[7] * X * Y + c[8] * Y * Z + c[9] * Z * X + c[10] * X * Y * Z)
+
+
+STATIONS = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.5], [0.8, 0.7, -0.6], [-0.9, 0.1, 0.85]])
+
+
+@pytest.mark.parametrize("name", list(HARMONIC))
+def test_harmonic_unbiased(name):
+    c = HARMONIC[name]
+    w = W.unit_box(STATIONS, g_kind="poly", poly=c, dt=0.02, paths=6000, clip=0, h=0.05)
+    r = oracle.solve(oracle_spec(w), w.stations, w.paths)
+    assert r.status == 0
+    for s, x in enumerate(w.stations):
+        want = poly_eval(c, x)
+        assert abs(r.u[s] - want) < 4 * r.se_u[s] + 1e-12, (s, r.u[s], want, r.se_u[s])
+        xp, xm = x + [0, 0, w.h], x - [0, 0, w.h]
+        want_d = (poly_eval(c, xp) - poly_eval(c, xm)) / (2 * w.h)
+        assert abs(r.gz[s] - want_d) < 4 * r.se_gz[s] + 1e-12, (s, r.gz[s], want_d, r.se_gz[s])
+
+
+def test_constant_density_quadratic_unbiased():
+    rho0 = 1.0
+    A = 2 * math.pi / 3 * rho0
+    w = W.unit_box(STATIONS, rho_kind="prism", rho0=rho0, g_kind="poly",
+                   poly=(0, 0, 0, 0, A, A, A, 0, 0, 0, 0), dt=0.02, paths=6000, clip=0, h=0.05)
+    r = oracle.solve(oracle_spec(w), w.stations, w.paths)
+    assert r.status == 0
+    for s, x in enumerate(w.stations):
+        assert abs(r.u[s] - A * np.dot(x, x)) < 4 * r.se_u[s], (s, r.u[s], A * np.dot(x, x), r.se_u[s])
+        assert abs(r.gz[s] - 2 * A * x[2]) < 4 * r.se_gz[s] + 1e-12
+
+
+def test_clipped_exit_points_lie_on_the_boundary():
+    """With clipping, every copy ends exactly on a face of the box and inside
+    the closed box (the segment is cut at its first crossing)."""
+    w = W.unit_box(STATIONS, g_kind="poly", poly=HARMONIC["linear"], dt=0.05, clip=1, h=0.05)
+    spec = oracle_spec(w)
+    lo, hi = np.array(w.lo), np.array(w.hi)
+    for s, x in enumerate(w.stations):
+        for p in range(200):
+            rc, u, steps, xe = oracle.walk_path(spec, x, s, p)
+            assert rc == 0
+            for c in range(3):
+                on_face = np.any((xe[c] == lo) | (xe[c] == hi))
+                assert on_face and np.all(xe[c] >= lo) and np.all(xe[c] <= hi)
+                assert u[c] == poly_eval(HARMONIC["linear"], xe[c])
+
+
+@pytest.mark.parametrize("clip", [0, 1])
+def test_brownian_scaling_R2(clip):
+    x0 = np.array([[0.2, -0.1, 0.3]])
+    base = W.unit_box(x0, rho_kind="prism", rho0=1.0, g_kind="zero", dt=0.01, paths=200, clip=clip)
+    R = 2.0
+    big = W.unit_box(x0 * R, rho_kind="prism", rho0=1.0, g_kind="zero", dt=0.01 * R * R, paths=200,
+                     clip=clip, half=R, h=0.05 * R)
+    a = oracle.solve(oracle_spec(base), base.stations, base.paths, per_path=True)
+    b = oracle.solve(oracle_spec(big), big.stations, big.paths, per_path=True)
+    np.testing.assert_array_equal(a.pp_copy_steps, b.pp_copy_steps)
+    np.testing.assert_allclose(b.pp_u, R * R * a.pp_u, rtol=1e-11, atol=0)
+
+
+def test_slab_exit_time_siegmund():
+    """Thin slab |z| < a (x, y walls far away): rho = 1, g = 0, no clipping
+    gives -u / (2 pi G) = N dt; E[N dt] = (a' - z)(a' + z), a' = a + beta s,
+    beta = -zeta(1/2)/sqrt(2 pi) = 0.5826, s = sigma sqrt(dt)."""
+    a, dt = 0.5, 4e-4
+    st = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.3]])
+    w = W.Workload(name="slab", lo=(-20.0, -20.0, -a), hi=(20.0, 20.0, a), rho_kind="prism",
+                   g_kind="zero", G=1.0, stations=st, dt=dt, h=0.01, seed=5, paths=4000,
+                   rho0=1.0, plo=(-100.0,) * 3, phi=(100.0,) * 3, clip=0, crn=0)
+    r = oracle.solve(oracle_spec(w), w.stations, w.paths)
+    beta = 0.5825971579390106
+    ap = a + beta * math.sqrt(dt)
+    for s, z in enumerate(st[:, 2]):
+        want = (ap - z) * (ap + z)
+        got = -r.u[s] / (2 * math.pi)
+        se = r.se_u[s] / (2 * math.pi)
+        # the correction is asymptotic; allow 4 SE plus 0.3 % model error
+        assert abs(got - want) < 4 * se + 3e-3 * want, (z, got, want, se)
+        # without the correction the error would be > 7 SE here
+        assert abs(got - (a - z) * (a + z)) > 4 * se
+
+
+# --- brute-force restatement (pure Python) ----------------------------------
+
+def _philox(ctr, key):
+    M0, M1, W0, W1 = 0xD2511F53, 0xCD9E8D57, 0x9E3779B9, 0xBB67AE85
+    c0, c1, c2, c3 = ctr
+    k0, k1 = key
+    for _ in range(10):
+        p0, p1 = M0 * c0, M1 * c2
+        c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0), p1 & 0xFFFFFFFF, ((p0 >> 32) ^ c3 ^ k1), p0 & 0xFFFFFFFF
+        k0, k1 = (k0 + W0) & 0xFFFFFFFF, (k1 + W1) & 0xFFFFFFFF
+    return [c0, c1, c2, c3]
+
+
+def _brute_path(w, x0, s, p):
+    lo, hi = w.lo, w.hi
+    sd = w.sigma * math.sqrt(w.dt)
+    M = 4 / 3 * math.pi * w.radius**3 * w.rho0
+
+    def rho(x):
+        return w.rho0 if x[0] ** 2 + x[1] ** 2 + x[2] ** 2 < w.radius**2 else 0.0
+
+    def g(x):
+        r = math.sqrt(x[0] ** 2 + x[1] ** 2 + x[2] ** 2)
+        return -w.G * M / r if r >= w.radius else -w.G * M * (3 * w.radius**2 - r * r) / (2 * w.radius**3)
+
+    key = [w.seed & 0xFFFFFFFF, w.seed >> 32]
+    offs = [0.0, w.h, -w.h]
+    out = []
+    for c in range(3):
+        Wp = list(x0)
+        X = [Wp[0], Wp[1], Wp[2] + offs[c]]
+        I, rp, n = 0.0, rho(X), 0
+        while True:
+            if n % 4 == 0:
+                words = []
+                for i in range(3):
+                    words += _philox([3 * (n // 4) + i, p, s, 0], key)
+                z = []
+                for i in range(6):
+                    u1, u2 = (words[2 * i] + 0.5) * 2.0**-32, (words[2 * i + 1] + 0.5) * 2.0**-32
+                    r = math.sqrt(-2 * math.log(u1))
+                    z += [r * math.cos(2 * math.pi * u2), r * math.sin(2 * math.pi * u2)]
+            m = n % 4
+            dW = [sd * z[3 * m + k] for k in range(3)]
+            Wn = [Wp[k] + dW[k] for k in range(3)]
+            X = [Wp[0], Wp[1], Wp[2] + offs[c]]
+            Y = [Wn[0], Wn[1], Wn[2] + offs[c]]
+            n += 1
+            if all(lo[k] < Y[k] < hi[k] for k in range(3)):
+                rn = rho(Y)
+                I += 0.5 * (rp + rn) * w.dt
+                rp = rn
+                Wp = Wn
+                continue
+            best, kb, bb = math.inf, -1, 0.0
+            for k in range(3):
+                if Y[k] <= lo[k]:
+                    b = lo[k]
+                elif Y[k] >= hi[k]:
+                    b = hi[k]
+                else:
+                    continue
+                t = (b - X[k]) / dW[k]
+                if t < best:
+                    best, kb, bb = t, k, b
+            th = min(max(best, 0.0), 1.0)
+            xs = [X[k] + th * dW[k] for k in range(3)]
+            xs[kb] = bb
+            I += 0.5 * (rp + rho(xs)) * th * w.dt
+            out.append((g(xs) - 2 * math.pi * w.G * I, n))
+            break
+    return out
+
+
+def test_brute_force_restatement_per_path():
+    w = W.sphere_line(paths=64, dt=1e-2)
+    spec = oracle_spec(w)
+    s = 2
+    for p in range(64):
+        rc, u, steps, _ = oracle.walk_path(spec, w.stations[s], s, p)
+        assert rc == 0
+        bf = _brute_path(w, list(w.stations[s]), s, p)
+        for c in range(3):
+            assert steps[c] == bf[c][1]
+            assert abs(u[c] - bf[c][0]) <= 1e-13 * abs(bf[c][0])
+
+
+def test_two_pass_statistics_match_numpy():
+    w = W.sphere_line(paths=3000, dt=4e-3)
+    r = oracle.solve(oracle_spec(w), w.stations[:3], w.paths, per_path=True)
+    for s in range(3):
+        np.testing.assert_allclose(r.u[s], r.pp_u[s].mean(), rtol=1e-14)
+        np.testing.assert_allclose(r.se_u[s], r.pp_u[s].std(ddof=1) / math.sqrt(w.paths), rtol=1e-12)
+        np.testing.assert_allclose(r.gz[s], r.pp_d[s].mean(), rtol=1e-12)
+        np.testing.assert_allclose(r.se_gz[s], r.pp_d[s].std(ddof=1) / math.sqrt(w.paths), rtol=1e-12)
+        assert r.path_steps[s] == r.pp_steps[s].sum()
+
+
+def test_station_on_boundary_rejected():
+    w = W.unit_box([[1.0, 0.0, 0.0]], g_kind="poly", poly=HARMONIC["linear"])
+    assert oracle.solve(oracle_spec(w), w.stations, 10).status == oracle.ERR_ARG
+    w = W.unit_box([[0.0, 0.0, 0.99]], g_kind="poly", poly=HARMONIC["linear"], h=0.05)
+    assert oracle.solve(oracle_spec(w), w.stations, 10).status == oracle.ERR_ARG
+
+
+def test_step_cap_reported():
+    w = W.unit_box([[0.0, 0.0, 0.0]], g_kind="poly", poly=HARMONIC["linear"], dt=1e-4)
+    assert oracle.solve(oracle_spec(w, max_steps=5), w.stations, 10).status == oracle.ERR_STEP_CAP
