@@ -1,0 +1,229 @@
+/*
+ * mcgrav.h -- C ABI of libmcgrav, a GB300 (sm_103a) Monte Carlo solver for
+ * the Newtonian potential and vertical gravity by the Feynman-Kac formula.
+ *
+ * Method: Donzelli, Bihlo, Kischinhevsky, Farquharson, "Massively parallel
+ * stochastic solution of the geophysical gravity problem" (arXiv:1709.07469).
+ *   - Problem (Sec. 2.1, Eq. 1 and its gravity form Eq. 4): a Dirichlet-
+ *     Poisson problem for the potential in a bounded domain.  This library
+ *     solves  Delta Phi = 4 pi G rho  in a box Omega with Dirichlet data g,
+ *     i.e. Phi = -u of the paper's sign convention (Eq. 4-5).
+ *   - Stochastic representation (Eq. 3, Eq. 5) with a standard Brownian
+ *     motion W (the paper's gamma = sqrt(2) W runs at twice the speed):
+ *       Phi(x0) = E[ g(W_tau) ] - 1/2 E[ int_0^tau 4 pi G rho(W_t) dt ].
+ *   - Walk (Sec. 2.3, steps 1-4): Euler-Maruyama increments of per-axis
+ *     standard deviation sigma sqrt(dt), trapezoid rule for the source
+ *     integral, exit when the walk is no longer strictly inside Omega.  The
+ *     last segment is clipped at its first crossing of the boundary and g is
+ *     read at the crossing point.
+ *   - Estimator (Eq. 7): the mean over N paths; g_z = dPhi/dz (Eq. 6) by the
+ *     centred difference of Sec. 4.2 with common random numbers: three walks
+ *     x0, x0 + h e_z, x0 - h e_z driven by the same increments.
+ *   - Random numbers: the paper names no generator.  Path p of station s
+ *     draws Philox4x32-10 (Salmon et al. 2011) with key (lo32 seed, hi32
+ *     seed) and counter (j, p, s, 0); step block b (steps 4b..4b+3) uses
+ *     j = 3b, 3b+1, 3b+2, whose 12 words give six Box-Muller pairs (cosine
+ *     first) = the 12 increments of the four steps.
+ *
+ * Conventions for every entry point:
+ *   - Status codes only; nothing is thrown across the ABI.  On error,
+ *     mcg_last_error() returns a thread-local message.
+ *   - "device" pointers are CUDA global memory of the current device,
+ *     "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer it passes; the library keeps no pointer after the call returns
+ *     (except inside the objects it creates, which say so).
+ *   - Calls taking a stream are asynchronous on that stream (0 = the legacy
+ *     default stream) unless documented as blocking.
+ *   - The result is a deterministic function of (seed, station index, path
+ *     index); it does not depend on batching, launch shape or what else is
+ *     in flight.
+ */
+#ifndef MCGRAV_H
+#define MCGRAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MCG_API __attribute__((visibility("default")))
+#else
+#define MCG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCG_OK = 0,
+    MCG_ERR_ARG = 1,        /* invalid argument (message says which)          */
+    MCG_ERR_OOM = 2,        /* device allocation failed                       */
+    MCG_ERR_CUDA = 3,       /* a CUDA runtime call failed                     */
+    MCG_ERR_STEP_CAP = 4,   /* a path exceeded max_steps (its value is NaN)   */
+    MCG_ERR_TIMEOUT = 5,    /* a bounded wait gave up                         */
+    MCG_ERR_NONFINITE = 6,  /* a per-path value was not finite                */
+    MCG_ERR_CANCELLED = 7   /* cancelled through the cancel flag              */
+} mcg_status;
+
+/* Box domain Omega = (lo, hi) (open).  Stations, and for g_z the two shifted
+ * copies x0 +- h e_z, must lie strictly inside. */
+typedef struct { double lo[3], hi[3]; } mcg_domain;
+
+typedef enum { MCG_RHO_NONE = 0, MCG_RHO_SPHERE = 1, MCG_RHO_PRISM = 2, MCG_RHO_VOXEL = 3 } mcg_rho_kind;
+
+/* Density model rho (kg/m^3 or any consistent unit), piecewise constant
+ * like the paper's cube model (Sec. 3).
+ *   SPHERE: rho0 where |x - center| < radius (strict), else 0.
+ *   PRISM : rho0 on the half-open box [lo, hi), else 0.
+ *   VOXEL : grid[ix + nx (iy + ny iz)] (float32, x fastest, DEVICE pointer)
+ *           on cells [origin + i spacing, origin + (i+1) spacing); 0 outside.
+ * G is the gravitational constant of the unit system (1 for nondimensional
+ * problems, 6.67430e-11 in SI). */
+typedef struct {
+    int32_t kind;
+    double G;
+    double rho0;
+    double center[3];
+    double radius;
+    double lo[3], hi[3];
+    const float* grid;
+    int64_t nx, ny, nz;
+    double origin[3], spacing[3];
+} mcg_density;
+
+typedef enum { MCG_G_ZERO = 0, MCG_G_SPHERE = 1, MCG_G_PRISM = 2, MCG_G_TABLE = 3, MCG_G_POLY = 4 } mcg_g_kind;
+
+/* Dirichlet data g on the boundary.
+ *   ZERO  : g = 0 (the paper's own choice, Sec. 2.2).
+ *   SPHERE: the analytic potential of the density's sphere.
+ *   PRISM : the analytic potential of the density's prism (Nagy's corner
+ *           function, the closed form the paper compares against).
+ *   TABLE : six node-centred float32 tables (DEVICE pointer) of nv x nu
+ *           nodes each (u fastest) in face order -x,+x,-y,+y,-z,+z; face
+ *           +-x is tabulated over (y, z), +-y over (x, z), +-z over (x, y),
+ *           nodes spanning the face edge to edge; read bilinearly.
+ *   POLY  : c0 + c1 x + c2 y + c3 z + c4 x^2 + c5 y^2 + c6 z^2 + c7 xy
+ *           + c8 yz + c9 zx + c10 xyz (test problems with known solutions). */
+typedef struct {
+    int32_t kind;
+    const float* faces;
+    int32_t nu, nv;
+    double poly[11];
+} mcg_boundary;
+
+typedef enum { MCG_FP64 = 0, MCG_MIXED = 1 } mcg_precision;
+
+/* Options.  Zero-initialise and set what you need; mcg_options_default()
+ * fills the defaults listed here. */
+typedef struct {
+    double h;                /* g_z finite-difference step (default 1e-2)          */
+    double sigma;            /* Brownian scale, step std = sigma sqrt(dt) (1)      */
+    int32_t precision;       /* MCG_FP64 plain walk or MCG_MIXED (default MIXED)   */
+    int32_t clip;            /* 1: clip last segment (default); 0: paper's full step */
+    int32_t crn_gz;          /* 1: three common-random-number walks, g_z (default)  */
+    int32_t block;           /* threads per block of the walk kernel (0 = auto)   */
+    int64_t max_steps;       /* RNG-step cap per path (default 2^31)               */
+    int64_t batch_paths;     /* paths per station per launch in mcgrav_solve (0 = auto) */
+    void* stream;            /* cudaStream_t (NULL = default stream)               */
+    volatile int32_t* cancel;/* optional host-mapped flag; nonzero stops new work   */
+} mcg_options;
+
+/* Per-station outputs (caller-owned, length S; any pointer may be NULL). */
+typedef struct {
+    double* u;               /* potential estimate Phi(x0)                        */
+    double* gz;              /* dPhi/dz estimate (NaN when crn_gz = 0)             */
+    double* se_u;            /* standard error of u                               */
+    double* se_gz;           /* standard error of gz                              */
+    int64_t* n_paths;        /* paths averaged                                    */
+    int64_t* path_steps;     /* Euler-Maruyama steps summed over paths and copies */
+} mcg_result;
+
+/* Running per-station statistics (device memory, 64 bytes each): two-pass
+ * batch statistics merged batch after batch with Chan's formula. */
+typedef struct {
+    double n;
+    double mean_u, m2_u;
+    double mean_d, m2_d;
+    double steps;            /* path-steps, exact below 2^53                      */
+    double pad[2];
+} mcg_station_state;
+
+MCG_API void mcg_options_default(mcg_options* o);
+MCG_API const char* mcg_last_error(void);
+MCG_API const char* mcg_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* One-call solver (Sec. 2.3 algorithm + Eq. 7 over all stations).          */
+/* ---------------------------------------------------------------------- */
+
+/* mcgrav_solve: estimates Phi and dPhi/dz at S stations from `paths` walks
+ * each (paths 0 .. paths-1 of each station's stream).
+ *   stations : HOST, S x 3 row-major (x, y, z).
+ *   density, boundary : grid / faces are DEVICE pointers when used.
+ *   out      : HOST arrays of length S.
+ * Blocking.  Allocates a device workspace of mcg_workspace_bytes(S,
+ * batch) for the duration of the call.  Returns MCG_ERR_STEP_CAP /
+ * MCG_ERR_NONFINITE when some path hit the cap / was not finite (the
+ * statistics then include NaN). */
+MCG_API int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+                 const double* stations, int64_t S, int64_t paths, double dt, uint64_t seed,
+                 const mcg_options* opts, mcg_result* out);
+
+/* ---------------------------------------------------------------------- */
+/* Device-resident building blocks (asynchronous on opts->stream).          */
+/* ---------------------------------------------------------------------- */
+
+/* mcg_walk: simulates paths p0 .. p0+N-1 of each of the S stations
+ * (Sec. 2.3 steps 1-4) and writes per-path values, item i = s N + (p - p0):
+ *   pp_u[i]     = g(x*) - 2 pi G I of the unshifted walk      (double)
+ *   pp_d[i]     = (u(+h) - u(-h)) / (2h), or NaN without crn_gz (double)
+ *   pp_steps[i] = Euler-Maruyama steps summed over the copies (int64)
+ *   stations_dev: DEVICE, S x 3.   pp_*: DEVICE, length S*N.
+ *   status_dev  : DEVICE int32, OR-ed with (1 << status) for every path that
+ *                 hit the step cap or produced a non-finite value; the
+ *                 caller zeroes it.
+ *   counter_dev : DEVICE uint64 work counter, zeroed by this call.
+ * Allocates nothing. */
+MCG_API int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+             const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
+             const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps,
+             int32_t* status_dev, unsigned long long* counter_dev);
+
+/* mcg_reduce: folds one batch of per-path values (S x N, as written by
+ * mcg_walk) into the running station states (Eq. 7 and the sample
+ * variance): per station a fixed-order two-pass mean / sum of squares with
+ * compensated partial sums, merged into states[s] with Chan's formula.
+ * states_dev: DEVICE, S entries; zero them before the first batch.
+ * Deterministic.  Allocates nothing. */
+MCG_API int mcg_reduce(const double* pp_u, const double* pp_d, const int64_t* pp_steps, int64_t S, int64_t N,
+               mcg_station_state* states_dev, void* stream);
+
+/* mcg_finalize: states -> u, gz, se = sqrt(M2 / (n-1) / n), n, steps.
+ * All output pointers DEVICE (may be NULL).  Allocates nothing. */
+MCG_API int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double* u, double* gz, double* se_u,
+                 double* se_gz, int64_t* n_paths, int64_t* path_steps, void* stream);
+
+/* Bytes of device workspace mcgrav_solve uses for S stations and batches of
+ * `batch` paths per station. */
+MCG_API size_t mcg_workspace_bytes(int64_t S, int64_t batch);
+
+/* ---------------------------------------------------------------------- */
+/* Random numbers (the generator the walks use), for verification.          */
+/* ---------------------------------------------------------------------- */
+
+/* mcg_philox: out[4i..4i+3] = Philox4x32-10(ctr[4i..4i+3], key[2i..2i+1]).
+ * All DEVICE pointers, n entries.  Allocates nothing. */
+MCG_API int mcg_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, void* stream);
+
+/* mcg_normals: the 12 normals of step blocks b0 .. b0+nblocks-1 of path
+ * (s, p), in the precision of the walk: precision MCG_FP64 writes doubles
+ * from u = (w + 1/2) 2^-32; MCG_MIXED writes floats from u = ((w >> 9) +
+ * 1/2) 2^-23 with the single-precision transcendental path of the mixed
+ * walk.  out: DEVICE, 12 * nblocks elements.  Allocates nothing. */
+MCG_API int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblocks, int32_t precision,
+                void* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCGRAV_H */

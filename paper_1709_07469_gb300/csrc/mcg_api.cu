@@ -1,0 +1,377 @@
+// mcg_api.cu -- the C ABI declared in include/mcgrav.h: argument checks, the
+// walk's launch parameters, and the one-call solver that runs walk ->
+// reduce batch by batch and copies the station results back.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "mcg_internal.h"
+#include "mcgrav.h"
+
+namespace mcg {
+
+namespace {
+thread_local char g_err[512] = "";
+
+constexpr double kPi = 3.14159265358979323846;
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return set_error(MCG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+int set_error(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+namespace {
+
+// Checks the problem description and fills the launch parameters (without
+// the work list, which the caller adds).
+int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B, double dt, uint64_t seed,
+                const mcg_options* o, WalkParams& P)
+{
+    if (!D || !R || !B || !o) return set_error(MCG_ERR_ARG, "null domain/density/boundary/options");
+    std::memset(&P, 0, sizeof(P));
+    if (!finite3(D->lo) || !finite3(D->hi)) return set_error(MCG_ERR_ARG, "domain bounds must be finite");
+    for (int k = 0; k < 3; ++k) {
+        if (!(D->lo[k] < D->hi[k])) return set_error(MCG_ERR_ARG, "domain lo[%d] >= hi[%d]", k, k);
+        P.lo[k] = D->lo[k];
+        P.hi[k] = D->hi[k];
+        P.cen[k] = 0.5 * (D->lo[k] + D->hi[k]);
+        P.half_f[k] = (float)(0.5 * (D->hi[k] - D->lo[k]));
+    }
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(MCG_ERR_ARG, "dt must be positive and finite");
+    if (!(o->sigma > 0.0) || !std::isfinite(o->sigma)) return set_error(MCG_ERR_ARG, "sigma must be positive");
+    if (o->crn_gz && !(o->h > 0.0)) return set_error(MCG_ERR_ARG, "h must be positive when crn_gz = 1");
+    if (o->precision != MCG_FP64 && o->precision != MCG_MIXED)
+        return set_error(MCG_ERR_ARG, "precision must be MCG_FP64 or MCG_MIXED");
+    if (o->max_steps <= 0) return set_error(MCG_ERR_ARG, "max_steps must be positive");
+    if (o->block != 0 && (o->block < 32 || o->block > 128 || o->block % 32 != 0))
+        return set_error(MCG_ERR_ARG, "block must be 0 or a multiple of 32 in [32, 128]");
+
+    P.rho_kind = R->kind;
+    P.G = R->G;
+    P.rho0 = R->rho0;
+    P.rho0_f = (float)R->rho0;
+    if (!std::isfinite(R->G)) return set_error(MCG_ERR_ARG, "G must be finite");
+    switch (R->kind) {
+    case MCG_RHO_NONE:
+        break;
+    case MCG_RHO_SPHERE:
+        if (!(R->radius > 0.0) || !finite3(R->center)) return set_error(MCG_ERR_ARG, "sphere radius/centre");
+        for (int k = 0; k < 3; ++k) {
+            P.sc[k] = R->center[k];
+            P.sc_f[k] = (float)(R->center[k] - P.cen[k]);
+        }
+        P.srad = R->radius;
+        P.srad2 = R->radius * R->radius;
+        P.srad2_f = (float)P.srad2;
+        break;
+    case MCG_RHO_PRISM:
+        for (int k = 0; k < 3; ++k) {
+            if (!(R->lo[k] < R->hi[k])) return set_error(MCG_ERR_ARG, "prism lo[%d] >= hi[%d]", k, k);
+            P.plo[k] = R->lo[k];
+            P.phi[k] = R->hi[k];
+            P.plo_f[k] = (float)(R->lo[k] - P.cen[k]);
+            P.phi_f[k] = (float)(R->hi[k] - P.cen[k]);
+        }
+        break;
+    case MCG_RHO_VOXEL: {
+        if (!R->grid) return set_error(MCG_ERR_ARG, "voxel grid pointer is null");
+        if (R->nx <= 0 || R->ny <= 0 || R->nz <= 0) return set_error(MCG_ERR_ARG, "voxel dims must be positive");
+        if ((double)R->nx * (double)R->ny * (double)R->nz >= 2147483647.0)
+            return set_error(MCG_ERR_ARG, "voxel grid too large (>= 2^31 cells)");
+        P.grid = R->grid;
+        P.nx = (int32_t)R->nx;
+        P.ny = (int32_t)R->ny;
+        P.nz = (int32_t)R->nz;
+        for (int k = 0; k < 3; ++k) {
+            if (!(R->spacing[k] > 0.0)) return set_error(MCG_ERR_ARG, "voxel spacing must be positive");
+            P.org[k] = R->origin[k];
+            P.sp[k] = R->spacing[k];
+            P.org_f[k] = (float)(R->origin[k] - P.cen[k]);
+            P.inv_sp_f[k] = (float)(1.0 / R->spacing[k]);
+        }
+        break;
+    }
+    default:
+        return set_error(MCG_ERR_ARG, "unknown density kind %d", R->kind);
+    }
+
+    P.g_kind = B->kind;
+    switch (B->kind) {
+    case MCG_G_ZERO:
+    case MCG_G_POLY:
+        break;
+    case MCG_G_SPHERE:
+        if (R->kind != MCG_RHO_SPHERE) return set_error(MCG_ERR_ARG, "MCG_G_SPHERE needs a sphere density");
+        break;
+    case MCG_G_PRISM:
+        if (R->kind != MCG_RHO_PRISM) return set_error(MCG_ERR_ARG, "MCG_G_PRISM needs a prism density");
+        break;
+    case MCG_G_TABLE:
+        if (!B->faces || B->nu < 2 || B->nv < 2) return set_error(MCG_ERR_ARG, "tables need faces and nu, nv >= 2");
+        if (!o->clip) return set_error(MCG_ERR_ARG, "tabulated boundary data needs clip = 1");
+        break;
+    default:
+        return set_error(MCG_ERR_ARG, "unknown boundary kind %d", B->kind);
+    }
+    P.faces = B->faces;
+    P.nu = B->nu;
+    P.nv = B->nv;
+    for (int i = 0; i < 11; ++i) P.poly[i] = B->poly[i];
+
+    P.dt = dt;
+    P.sd = o->sigma * std::sqrt(dt);
+    P.h = o->crn_gz ? o->h : 0.0;
+    P.two_pi_G = 2.0 * kPi * R->G;
+    P.sd_f = (float)P.sd;
+    P.h_f = (float)P.h;
+    P.lnscale_f = (float)(-2.0 * std::log(2.0) * P.sd * P.sd);
+    P.crn = o->crn_gz ? 1 : 0;
+    P.clip = o->clip ? 1 : 0;
+    P.max_steps = o->max_steps;
+    P.key0 = (uint32_t)seed;
+    P.key1 = (uint32_t)(seed >> 32);
+    P.cancel = o->cancel;
+    return MCG_OK;
+}
+
+int check_station(const WalkParams& P, const double* x, int64_t s)
+{
+    if (!finite3(x)) return set_error(MCG_ERR_ARG, "station %lld is not finite", (long long)s);
+    const double off[3] = {0.0, P.h, -P.h};
+    for (int c = 0; c < (P.crn ? 3 : 1); ++c) {
+        const double y[3] = {x[0], x[1], x[2] + off[c]};
+        for (int k = 0; k < 3; ++k)
+            if (!(y[k] > P.lo[k] && y[k] < P.hi[k]))
+                return set_error(MCG_ERR_ARG, "station %lld (copy %d) is not strictly inside the domain",
+                                 (long long)s, c);
+    }
+    return MCG_OK;
+}
+
+int status_from_bits(int bits)
+{
+    if (bits & (1 << MCG_ERR_ARG)) return set_error(MCG_ERR_ARG, "a station lies on or outside the domain");
+    if (bits & (1 << MCG_ERR_STEP_CAP)) return set_error(MCG_ERR_STEP_CAP, "a path exceeded max_steps");
+    if (bits & (1 << MCG_ERR_NONFINITE)) return set_error(MCG_ERR_NONFINITE, "a per-path value was not finite");
+    if (bits & (1 << MCG_ERR_CANCELLED)) return set_error(MCG_ERR_CANCELLED, "cancelled");
+    return MCG_OK;
+}
+
+}  // namespace
+}  // namespace mcg
+
+using namespace mcg;
+
+extern "C" {
+
+void mcg_options_default(mcg_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->h = 1e-2;
+    o->sigma = 1.0;
+    o->precision = MCG_MIXED;
+    o->clip = 1;
+    o->crn_gz = 1;
+    o->block = 0;
+    o->max_steps = (int64_t)1 << 31;
+    o->batch_paths = 0;
+    o->stream = nullptr;
+    o->cancel = nullptr;
+}
+
+const char* mcg_last_error(void) { return g_err; }
+
+const char* mcg_version(void) { return "mcgrav 0.1 sm_103a"; }
+
+size_t mcg_workspace_bytes(int64_t S, int64_t batch)
+{
+    if (S <= 0 || batch <= 0) return 0;
+    const size_t s = (size_t)S, n = (size_t)S * (size_t)batch;
+    return align256(s * 3 * sizeof(double)) + align256(s * sizeof(mcg_station_state)) + 256 /* status+counter */ +
+           align256(s * 6 * sizeof(double)) + 2 * align256(n * sizeof(double)) + align256(n * sizeof(int64_t));
+}
+
+int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+             const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
+             const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps, int32_t* status_dev,
+             unsigned long long* counter_dev)
+{
+    WalkParams P;
+    int rc = make_params(domain, density, boundary, dt, seed, opts, P);
+    if (rc) return rc;
+    if (S < 0 || N < 0 || p0 < 0) return set_error(MCG_ERR_ARG, "S, N and p0 must be non-negative");
+    if (p0 + N > (int64_t)1 << 32) return set_error(MCG_ERR_ARG, "path indices must fit in 32 bits");
+    if (S > (int64_t)1 << 32) return set_error(MCG_ERR_ARG, "station indices must fit in 32 bits");
+    if (S == 0 || N == 0) return MCG_OK;
+    if (!stations_dev || !pp_u || !pp_d || !pp_steps || !status_dev || !counter_dev)
+        return set_error(MCG_ERR_ARG, "null device buffer");
+    P.stations = stations_dev;
+    P.S = S;
+    P.N = N;
+    P.p0 = p0;
+    P.total = (unsigned long long)S * (unsigned long long)N;
+    P.pp_u = pp_u;
+    P.pp_d = pp_d;
+    P.pp_steps = pp_steps;
+    P.status = status_dev;
+    P.counter = counter_dev;
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+    e = launch_walk(P, opts->precision, opts->block ? opts->block : 128, st);
+    if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+    return MCG_OK;
+}
+
+int mcg_reduce(const double* pp_u, const double* pp_d, const int64_t* pp_steps, int64_t S, int64_t N,
+               mcg_station_state* states_dev, void* stream)
+{
+    if (S < 0 || N < 0) return set_error(MCG_ERR_ARG, "S and N must be non-negative");
+    if (S == 0 || N == 0) return MCG_OK;
+    if (!pp_u || !pp_d || !pp_steps || !states_dev) return set_error(MCG_ERR_ARG, "null device buffer");
+    if (S > 2147483647LL) return set_error(MCG_ERR_ARG, "too many stations for one reduction");
+    cudaError_t e = launch_reduce(pp_u, pp_d, pp_steps, S, N, states_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? MCG_OK : cuda_fail(e, "reduce kernel launch");
+}
+
+int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double* u, double* gz, double* se_u,
+                 double* se_gz, int64_t* n_paths, int64_t* path_steps, void* stream)
+{
+    if (S < 0) return set_error(MCG_ERR_ARG, "S must be non-negative");
+    if (S == 0) return MCG_OK;
+    if (!states_dev) return set_error(MCG_ERR_ARG, "null states");
+    cudaError_t e = launch_finalize(states_dev, S, u, gz, se_u, se_gz, n_paths, path_steps, (cudaStream_t)stream);
+    return e == cudaSuccess ? MCG_OK : cuda_fail(e, "finalize kernel launch");
+}
+
+int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+                 const double* stations, int64_t S, int64_t paths, double dt, uint64_t seed,
+                 const mcg_options* opts_in, mcg_result* out)
+{
+    mcg_options opts;
+    if (opts_in) opts = *opts_in;
+    else mcg_options_default(&opts);
+    WalkParams P;
+    int rc = make_params(domain, density, boundary, dt, seed, &opts, P);
+    if (rc) return rc;
+    if (S < 0 || paths <= 0) return set_error(MCG_ERR_ARG, "need S >= 0 and paths >= 1");
+    if (paths > (int64_t)1 << 32) return set_error(MCG_ERR_ARG, "paths must fit in 32 bits");
+    if (S > 0 && (!stations || !out)) return set_error(MCG_ERR_ARG, "null stations or result");
+    for (int64_t s = 0; s < S; ++s)
+        if ((rc = check_station(P, stations + 3 * s, s))) return rc;
+    if (S == 0) return MCG_OK;
+
+    int64_t batch = opts.batch_paths;
+    if (batch <= 0) {
+        // per-path buffers of at most ~4 GiB per launch
+        const int64_t cap = (int64_t)((4ull << 30) / (24ull * (unsigned long long)S));
+        batch = paths < cap ? paths : (cap > 0 ? cap : 1);
+    }
+    if (batch > paths) batch = paths;
+    const size_t bytes = mcg_workspace_bytes(S, batch);
+    char* ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MCG_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    cudaStream_t st = (cudaStream_t)opts.stream;
+    const size_t s_ = (size_t)S, n_ = (size_t)S * (size_t)batch;
+    char* q = ws;
+    double* d_st = (double*)q;
+    q += align256(s_ * 3 * sizeof(double));
+    mcg_station_state* d_state = (mcg_station_state*)q;
+    q += align256(s_ * sizeof(mcg_station_state));
+    int32_t* d_status = (int32_t*)q;
+    unsigned long long* d_counter = (unsigned long long*)(q + 128);
+    q += 256;
+    double* d_res = (double*)q;
+    q += align256(s_ * 6 * sizeof(double));
+    double* d_u = (double*)q;
+    q += align256(n_ * sizeof(double));
+    double* d_d = (double*)q;
+    q += align256(n_ * sizeof(double));
+    int64_t* d_steps = (int64_t*)q;
+
+    double* h_res = new double[6 * s_];
+    int32_t h_status = 0;
+    rc = MCG_OK;
+    do {
+        if ((e = cudaMemcpyAsync(d_st, stations, s_ * 3 * sizeof(double), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemsetAsync(d_state, 0, s_ * sizeof(mcg_station_state), st)) ||
+            (e = cudaMemsetAsync(d_status, 0, 256, st))) {
+            rc = cuda_fail(e, "workspace initialisation");
+            break;
+        }
+        for (int64_t p0 = 0; p0 < paths && rc == MCG_OK; p0 += batch) {
+            const int64_t nb = (paths - p0) < batch ? (paths - p0) : batch;
+            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &opts, d_u, d_d, d_steps, d_status,
+                          d_counter);
+            if (rc == MCG_OK) rc = mcg_reduce(d_u, d_d, d_steps, S, nb, d_state, st);
+        }
+        if (rc) break;
+        rc = mcg_finalize(d_state, S, d_res, d_res + s_, d_res + 2 * s_, d_res + 3 * s_, (int64_t*)(d_res + 4 * s_),
+                          (int64_t*)(d_res + 5 * s_), st);
+        if (rc) break;
+        if ((e = cudaMemcpyAsync(h_res, d_res, 6 * s_ * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(&h_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            rc = cuda_fail(e, "result copy");
+            break;
+        }
+        for (int64_t s = 0; s < S; ++s) {
+            if (out->u) out->u[s] = h_res[s];
+            if (out->gz) out->gz[s] = opts.crn_gz ? h_res[s_ + s] : NAN;
+            if (out->se_u) out->se_u[s] = h_res[2 * s_ + s];
+            if (out->se_gz) out->se_gz[s] = opts.crn_gz ? h_res[3 * s_ + s] : NAN;
+            if (out->n_paths) std::memcpy(&out->n_paths[s], &h_res[4 * s_ + s], sizeof(int64_t));
+            if (out->path_steps) std::memcpy(&out->path_steps[s], &h_res[5 * s_ + s], sizeof(int64_t));
+        }
+        rc = status_from_bits(h_status);
+    } while (0);
+    if (rc == MCG_ERR_CUDA) cudaStreamSynchronize(st);
+    delete[] h_res;
+    cudaFree(ws);
+    return rc;
+}
+
+int mcg_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, void* stream)
+{
+    if (n < 0) return set_error(MCG_ERR_ARG, "n must be non-negative");
+    if (n == 0) return MCG_OK;
+    if (!ctr || !key || !out) return set_error(MCG_ERR_ARG, "null device buffer");
+    cudaError_t e = launch_philox(ctr, key, n, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? MCG_OK : cuda_fail(e, "philox kernel launch");
+}
+
+int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblocks, int32_t precision, void* out,
+                void* stream)
+{
+    if (nblocks < 0) return set_error(MCG_ERR_ARG, "nblocks must be non-negative");
+    if (precision != MCG_FP64 && precision != MCG_MIXED) return set_error(MCG_ERR_ARG, "bad precision");
+    if (nblocks == 0) return MCG_OK;
+    if (!out) return set_error(MCG_ERR_ARG, "null output");
+    cudaError_t e = launch_normals(seed, s, p, b0, nblocks, precision, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? MCG_OK : cuda_fail(e, "normals kernel launch");
+}
+
+}  // extern "C"

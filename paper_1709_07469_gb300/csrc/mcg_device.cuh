@@ -1,0 +1,268 @@
+// mcg_device.cuh -- device functions of the walk: Philox4x32-10, Box-Muller
+// in double and single precision, density samplers, boundary data.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mcg_internal.h"
+
+namespace mcg {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies of counter words 0 and 2; the high halves are xor-ed
+// with words 1 / 3 and the round key, which advances by the Weyl constants.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Double precision normals (the plain FP64 walk): u = (w + 1/2) 2^-32,
+// r = sqrt(-2 ln u1), angle 2 pi u2, cosine first.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double u01_f64(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+__device__ __forceinline__ void box_muller_f64(uint32_t w1, uint32_t w2, double& z0, double& z1)
+{
+    const double r = sqrt(-2.0 * log(u01_f64(w1)));
+    const double a = 2.0 * 3.14159265358979323846 * u01_f64(w2);
+    double sn, cs;
+    sincos(a, &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
+__device__ __forceinline__ void normals12_f64(uint32_t s, uint32_t p, uint32_t b, uint32_t k0, uint32_t k1,
+                                              double z[12])
+{
+#pragma unroll
+    for (uint32_t i = 0; i < 3; ++i) {
+        const uint4 w = philox4x32_10(make_uint4(3u * b + i, p, s, 0u), k0, k1);
+        box_muller_f64(w.x, w.y, z[4 * i], z[4 * i + 1]);
+        box_muller_f64(w.z, w.w, z[4 * i + 2], z[4 * i + 3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single precision normals (the mixed walk).  u = ((w >> 9) + 1/2) 2^-23 is
+// built exactly from the mantissa bits: 1 + (w >> 9) 2^-23 minus the float
+// just below 1.  The radius uses the hardware base-2 logarithm and square
+// root; the angle 2 pi u2 is taken as pi + 2 pi (u2 - 1/2) so the sine and
+// cosine approximations see (-pi, pi): cos(2 pi u2) = -cos(a), sin(2 pi u2)
+// = -sin(a).  `lnscale` = -2 ln 2 sd^2 folds the step scale into r.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float u01_f32(uint32_t w)
+{
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994f;
+}
+// u - 1/2, exact: (1 + m 2^-23) - 1.5 is exact, + 2^-24 lands on the grid.
+__device__ __forceinline__ float u01m_f32(uint32_t w)
+{
+    return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.5f) + 0x1p-24f;
+}
+
+__device__ __forceinline__ void box_muller_f32(uint32_t w1, uint32_t w2, float lnscale, float& z0, float& z1)
+{
+    const float nr = -sqrt_approx(lnscale * lg2_approx(u01_f32(w1)));  // -sd sqrt(-2 ln u1)
+    const float a = 6.28318530717958648f * u01m_f32(w2);
+    z0 = nr * cos_approx(a);
+    z1 = nr * sin_approx(a);
+}
+
+__device__ __forceinline__ void normals12_f32(uint32_t s, uint32_t p, uint32_t b, uint32_t k0, uint32_t k1,
+                                              float lnscale, float z[12])
+{
+#pragma unroll
+    for (uint32_t i = 0; i < 3; ++i) {
+        const uint4 w = philox4x32_10(make_uint4(3u * b + i, p, s, 0u), k0, k1);
+        box_muller_f32(w.x, w.y, lnscale, z[4 * i], z[4 * i + 1]);
+        box_muller_f32(w.z, w.w, lnscale, z[4 * i + 2], z[4 * i + 3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Density samplers.
+// ---------------------------------------------------------------------------
+template <int RHO>
+__device__ __forceinline__ float rho_f32(const WalkParams& P, float x, float y, float z)
+{
+    if constexpr (RHO == MCG_RHO_SPHERE) {
+        const float dx = x - P.sc_f[0], dy = y - P.sc_f[1], dz = z - P.sc_f[2];
+        return (dx * dx + dy * dy + dz * dz < P.srad2_f) ? P.rho0_f : 0.0f;
+    } else if constexpr (RHO == MCG_RHO_PRISM) {
+        const bool in = x >= P.plo_f[0] && x < P.phi_f[0] && y >= P.plo_f[1] && y < P.phi_f[1] &&
+                        z >= P.plo_f[2] && z < P.phi_f[2];
+        return in ? P.rho0_f : 0.0f;
+    } else if constexpr (RHO == MCG_RHO_VOXEL) {
+        const float tx = floorf((x - P.org_f[0]) * P.inv_sp_f[0]);
+        const float ty = floorf((y - P.org_f[1]) * P.inv_sp_f[1]);
+        const float tz = floorf((z - P.org_f[2]) * P.inv_sp_f[2]);
+        const bool in = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny && tz >= 0.f &&
+                        tz < (float)P.nz;
+        if (!in) return 0.0f;
+        const int idx = (int)tx + P.nx * ((int)ty + P.ny * (int)tz);
+        return __ldg(P.grid + idx);
+    } else {
+        return 0.0f;
+    }
+}
+
+// Double precision density at an absolute point (same cells as above).
+__device__ __forceinline__ double rho_f64(const WalkParams& P, const double x[3])
+{
+    switch (P.rho_kind) {
+    case MCG_RHO_SPHERE: {
+        const double dx = __dadd_rn(x[0], -P.sc[0]), dy = __dadd_rn(x[1], -P.sc[1]),
+                     dz = __dadd_rn(x[2], -P.sc[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        return r2 < P.srad2 ? P.rho0 : 0.0;
+    }
+    case MCG_RHO_PRISM:
+        for (int k = 0; k < 3; ++k)
+            if (!(x[k] >= P.plo[k] && x[k] < P.phi[k])) return 0.0;
+        return P.rho0;
+    case MCG_RHO_VOXEL: {
+        int idx[3];
+        const int n[3] = {P.nx, P.ny, P.nz};
+        for (int k = 0; k < 3; ++k) {
+            const double t = floor(__ddiv_rn(__dadd_rn(x[k], -P.org[k]), P.sp[k]));
+            if (!(t >= 0.0 && t < (double)n[k])) return 0.0;
+            idx[k] = (int)t;
+        }
+        return (double)__ldg(P.grid + idx[0] + P.nx * (idx[1] + P.ny * idx[2]));
+    }
+    default:
+        return 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary data (double precision, evaluated once per copy at its exit).
+// ---------------------------------------------------------------------------
+// log(t + r), r = |(t, p, q)|, stable for t < 0 via (p^2 + q^2) / (r - t).
+__device__ __forceinline__ double log_tr(double t, double p, double q, double r)
+{
+    return t >= 0.0 ? log(t + r) : log(p * p + q * q) - log(r - t);
+}
+
+// Nagy's corner function of the prism potential; terms with a vanishing
+// polynomial prefactor are their limit 0.
+static __device__ __noinline__ double prism_corner(double x, double y, double z)
+{
+    const double r = sqrt(x * x + y * y + z * z);
+    if (r == 0.0) return 0.0;
+    double f = 0.0;
+    if (x * y != 0.0) f += x * y * log_tr(z, x, y, r);
+    if (y * z != 0.0) f += y * z * log_tr(x, y, z, r);
+    if (z * x != 0.0) f += z * x * log_tr(y, z, x, r);
+    if (x != 0.0) f -= 0.5 * x * x * atan(y * z / (x * r));
+    if (y != 0.0) f -= 0.5 * y * y * atan(z * x / (y * r));
+    if (z != 0.0) f -= 0.5 * z * z * atan(x * y / (z * r));
+    return f;
+}
+
+// Phi of a homogeneous prism [lo, hi) at x: -G rho times the alternating
+// corner sum (+ at the all-upper corner).
+__device__ __forceinline__ double prism_potential(double G, double rho, const double lo[3], const double hi[3],
+                                                  const double x[3])
+{
+    double s = 0.0;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        const int i = c & 1, j = (c >> 1) & 1, k = (c >> 2) & 1;
+        const double f = prism_corner((i ? hi[0] : lo[0]) - x[0], (j ? hi[1] : lo[1]) - x[1],
+                                      (k ? hi[2] : lo[2]) - x[2]);
+        s += ((3 - i - j - k) & 1) ? -f : f;
+    }
+    return -G * rho * s;
+}
+
+__device__ __forceinline__ double sphere_potential(const WalkParams& P, const double x[3])
+{
+    const double dx = x[0] - P.sc[0], dy = x[1] - P.sc[1], dz = x[2] - P.sc[2];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double a = P.srad, a2 = a * a;
+    const double M = 4.0 / 3.0 * 3.14159265358979323846 * a * a * a * P.rho0;
+    if (r >= a) return -P.G * M / r;
+    return -P.G * M * (3.0 * a2 - r * r) / (2.0 * a2 * a);
+}
+
+// Bilinear read of face `face` (0..5) at the absolute boundary point x.
+__device__ __forceinline__ double table_value(const WalkParams& P, int face, const double x[3])
+{
+    const int k = face >> 1;
+    const int a = (k == 0) ? 1 : 0, b = (k == 2) ? 1 : 2;
+    const float* t = P.faces + (int64_t)face * P.nu * P.nv;
+    const double tu = (x[a] - P.lo[a]) / (P.hi[a] - P.lo[a]) * (double)(P.nu - 1);
+    const double tv = (x[b] - P.lo[b]) / (P.hi[b] - P.lo[b]) * (double)(P.nv - 1);
+    const double fu = fmin(fmax(floor(tu), 0.0), (double)(P.nu - 2));
+    const double fv = fmin(fmax(floor(tv), 0.0), (double)(P.nv - 2));
+    const int iu = (int)fu, iv = (int)fv;
+    const double au = tu - fu, av = tv - fv;
+    const float* r0 = t + (int64_t)P.nu * iv + iu;
+    const double f00 = __ldg(r0), f10 = __ldg(r0 + 1), f01 = __ldg(r0 + P.nu), f11 = __ldg(r0 + P.nu + 1);
+    return (1.0 - au) * (1.0 - av) * f00 + au * (1.0 - av) * f10 + (1.0 - au) * av * f01 + au * av * f11;
+}
+
+// g at the absolute exit point x on face `face` (-1 if not on a face).
+static __device__ __noinline__ double boundary_value(const WalkParams& P, int face, const double* x)
+{
+    switch (P.g_kind) {
+    case MCG_G_SPHERE:
+        return sphere_potential(P, x);
+    case MCG_G_PRISM:
+        return prism_potential(P.G, P.rho0, P.plo, P.phi, x);
+    case MCG_G_TABLE:
+        return face < 0 ? __longlong_as_double(0x7ff8000000000000LL) : table_value(P, face, x);
+    case MCG_G_POLY: {
+        const double* c = P.poly;
+        const double X = x[0], Y = x[1], Z = x[2];
+        return c[0] + c[1] * X + c[2] * Y + c[3] * Z + c[4] * X * X + c[5] * Y * Y + c[6] * Z * Z +
+               c[7] * X * Y + c[8] * Y * Z + c[9] * Z * X + c[10] * X * Y * Z;
+    }
+    default:
+        return 0.0;
+    }
+}
+
+}  // namespace mcg

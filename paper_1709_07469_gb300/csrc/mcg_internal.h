@@ -1,0 +1,72 @@
+// mcg_internal.h -- launch parameters shared by the translation units of
+// libmcgrav (host side of the C ABI and the kernels).  Not part of the ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mcgrav.h"
+
+namespace mcg {
+
+// Everything one walk launch needs, passed by value as a kernel parameter.
+// Coordinates of the mixed-precision walk are relative to the box centre
+// (`cen`), so the exit test is |x_k| < half_k; the FP64 walk uses absolute
+// coordinates exactly as the problem states them.
+struct WalkParams {
+    // domain
+    double lo[3], hi[3], cen[3];
+    float half_f[3];
+    // density
+    int32_t rho_kind;
+    double G, rho0;
+    float rho0_f;
+    double sc[3], srad, srad2;     // sphere centre, radius, radius^2 (absolute)
+    float sc_f[3], srad2_f;        // sphere centre relative to cen
+    double plo[3], phi[3];         // prism (absolute)
+    float plo_f[3], phi_f[3];      // prism relative to cen
+    const float* grid;
+    int32_t nx, ny, nz;
+    double org[3], sp[3];          // voxel origin / spacing (absolute)
+    float org_f[3], inv_sp_f[3];   // origin relative to cen, 1/spacing
+    // boundary data
+    int32_t g_kind;
+    const float* faces;
+    int32_t nu, nv;
+    double poly[11];
+    // walk
+    double dt, sd, h, two_pi_G;
+    float sd_f, h_f, lnscale_f;    // lnscale_f = -2 ln 2 sd^2
+    int32_t crn, clip;
+    int64_t max_steps;
+    uint32_t key0, key1;
+    // work list: item i -> station i / N, path p0 + i % N
+    const double* stations;
+    int64_t S, N, p0;
+    unsigned long long total;
+    double* pp_u;
+    double* pp_d;
+    int64_t* pp_steps;
+    int32_t* status;
+    unsigned long long* counter;
+    volatile int32_t* cancel;
+};
+
+// Kernel launchers (mcg_walk.cu).
+cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStream_t st);
+int walk_blocks_per_sm(int precision, int rho_kind, int block);
+
+// Reduction launchers (mcg_reduce.cu).
+cudaError_t launch_reduce(const double* pp_u, const double* pp_d, const int64_t* pp_steps, int64_t S,
+                          int64_t N, mcg_station_state* states, cudaStream_t st);
+cudaError_t launch_finalize(const mcg_station_state* states, int64_t S, double* u, double* gz, double* se_u,
+                            double* se_gz, int64_t* n_paths, int64_t* path_steps, cudaStream_t st);
+
+// RNG launchers (mcg_rng.cu).
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblocks, int precision,
+                           void* out, cudaStream_t st);
+
+// Thread-local error message (mcg_api.cu).
+int set_error(int code, const char* fmt, ...);
+
+}  // namespace mcg

@@ -1,0 +1,442 @@
+// mcg_walk.cu -- the walk kernels (Sec. 2.3 of the paper, steps 1-4).
+//
+// Both kernels are persistent: every warp keeps 32 walks in flight and, as
+// walks exit, refills the free lanes from a global work counter with one
+// warp-aggregated atomic (__ballot_sync / __shfl_sync), so lanes do not idle
+// behind the long exit-time tail.  A lane owns one path (station s, path p)
+// and its common-random-number copies x0, x0 + h e_z, x0 - h e_z, which share
+// every Gaussian increment.  Random numbers come four steps at a time: three
+// Philox4x32-10 calls -> twelve normals -> four Euler-Maruyama steps.
+//
+//  * walk_fp64_kernel : the plain double-precision walk; its arithmetic
+//    follows the problem statement operation by operation (no contraction)
+//    so that a path agrees with a plain double-precision evaluation to
+//    rounding of the transcendental functions.
+//  * walk_mixed_kernel: single-precision stepping, random-number transform
+//    and density lookup; the source integral keeps single-precision partial
+//    sums over at most 64 steps which are flushed into a double accumulator;
+//    the exit-segment clip, the boundary value and the per-path estimate are
+//    double precision.
+#include <cuda_runtime.h>
+
+#include "mcg_device.cuh"
+#include "mcg_internal.h"
+
+namespace mcg {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kNaN = __builtin_nan("");
+
+// Claims new items for the lanes of this warp that are free.  Returns the
+// claimed item in `item`; lanes beyond the end of the work list become
+// `exhausted`.
+__device__ __forceinline__ bool refill(const WalkParams& P, bool busy, bool& exhausted,
+                                       unsigned long long& item)
+{
+    const unsigned want = __ballot_sync(kFull, !busy && !exhausted);
+    if (want == 0u) return false;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(want) - 1;
+    unsigned long long base = 0ull;
+    if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(want));
+    base = __shfl_sync(kFull, base, leader);
+    if (busy || exhausted) return false;
+    item = base + (unsigned long long)__popc(want & ((1u << lane) - 1u));
+    if (item >= P.total) {
+        exhausted = true;
+        return false;
+    }
+    return true;
+}
+
+// A station whose walk copies are not all strictly inside Omega gets NaN
+// and the MCG_ERR_ARG bit (mcgrav_solve rejects such stations up front).
+__device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsigned long long item)
+{
+    const double x = P.stations[3 * s], y = P.stations[3 * s + 1], z = P.stations[3 * s + 2];
+    const bool ok = x > P.lo[0] && x < P.hi[0] && y > P.lo[1] && y < P.hi[1] && z - P.h > P.lo[2] &&
+                    z + P.h < P.hi[2] && z > P.lo[2] && z < P.hi[2];
+    if (!ok) {
+        P.pp_u[item] = kNaN;
+        P.pp_d[item] = kNaN;
+        P.pp_steps[item] = 0;
+        atomicOr(P.status, 1 << MCG_ERR_ARG);
+    }
+    return ok;
+}
+
+__device__ __forceinline__ bool cancelled(const WalkParams& P)
+{
+    int c = 0;
+    if ((threadIdx.x & 31) == 0 && P.cancel != nullptr) c = *P.cancel;
+    return __shfl_sync(kFull, c, 0) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Exit handling (double precision).  X: last inside point, Y: first point
+// not strictly inside, both as the walk computed them.  Clips the segment at
+// its first boundary crossing (lowest axis on ties), closes the trapezoid
+// over the clipped part and returns g(x*) - 2 pi G I.
+// ---------------------------------------------------------------------------
+__device__ __noinline__ double exit_fp64(const WalkParams& P, const double* X, const double* dW,
+                                         const double* Y, double I, double rp)
+{
+    double xs[3];
+    double theta = 1.0;
+    int face = -1;
+    if (P.clip) {
+        int kstar = -1;
+        double tmin = __longlong_as_double(0x7ff0000000000000LL), bstar = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double b;
+            if (Y[k] <= P.lo[k]) b = P.lo[k];
+            else if (Y[k] >= P.hi[k]) b = P.hi[k];
+            else continue;
+            const double t = __ddiv_rn(__dadd_rn(b, -X[k]), dW[k]);
+            if (t < tmin) {
+                tmin = t;
+                kstar = k;
+                bstar = b;
+            }
+        }
+        if (kstar < 0) return kNaN;
+        theta = fmin(fmax(tmin, 0.0), 1.0);
+        for (int k = 0; k < 3; ++k) xs[k] = __dadd_rn(X[k], __dmul_rn(theta, dW[k]));
+        xs[kstar] = bstar;
+        face = 2 * kstar + (bstar == P.hi[kstar] ? 1 : 0);
+    } else {
+        xs[0] = Y[0];
+        xs[1] = Y[1];
+        xs[2] = Y[2];
+    }
+    const double r = rho_f64(P, xs);
+    I = __dadd_rn(I, __dmul_rn(__dmul_rn(__dmul_rn(0.5, __dadd_rn(rp, r)), theta), P.dt));
+    return __dadd_rn(boundary_value(P, face, xs), -__dmul_rn(P.two_pi_G, I));
+}
+
+// Mixed walk: X, Y relative to the box centre in single precision; `acc`
+// is the flushed + partial sum S = rho_0 / 2 + sum_{n=1}^{N-1} rho_n, so the
+// trapezoid integral over the inside steps is dt (S - rho_{N-1} / 2).
+__device__ __noinline__ double exit_mixed(const WalkParams& P, float x0, float x1, float x2, float y0, float y1,
+                                          float y2, double acc, float rp)
+{
+    const float Xf[3] = {x0, x1, x2}, Yf[3] = {y0, y1, y2};
+    double X[3], dW[3], xs[3];
+    for (int k = 0; k < 3; ++k) {
+        X[k] = (double)Xf[k];
+        dW[k] = (double)Yf[k] - (double)Xf[k];
+    }
+    double theta = 1.0;
+    int face = -1;
+    if (P.clip) {
+        int kstar = -1;
+        double tmin = __longlong_as_double(0x7ff0000000000000LL), bstar = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            if (!(fabsf(Yf[k]) >= P.half_f[k])) continue;  // the test that ended the walk
+            const double b = (Yf[k] > 0.f ? P.hi[k] : P.lo[k]) - P.cen[k];
+            const double t = (b - X[k]) / dW[k];
+            if (t < tmin) {
+                tmin = t;
+                kstar = k;
+                bstar = b;
+            }
+        }
+        if (kstar < 0) return kNaN;
+        theta = fmin(fmax(tmin, 0.0), 1.0);
+        for (int k = 0; k < 3; ++k) xs[k] = P.cen[k] + (X[k] + theta * dW[k]);
+        const bool upper = Yf[kstar] > 0.f;
+        xs[kstar] = upper ? P.hi[kstar] : P.lo[kstar];
+        face = 2 * kstar + (upper ? 1 : 0);
+        (void)bstar;
+    } else {
+        for (int k = 0; k < 3; ++k) xs[k] = P.cen[k] + (double)Yf[k];
+    }
+    const double r = rho_f64(P, xs);
+    const double rpd = (double)rp;
+    const double I = P.dt * (acc - 0.5 * rpd) + 0.5 * theta * P.dt * (rpd + r);
+    return boundary_value(P, face, xs) - P.two_pi_G * I;
+}
+
+__device__ __forceinline__ void write_path(const WalkParams& P, unsigned long long item, double u0, double up,
+                                           double um, int64_t steps)
+{
+    const double d = P.crn ? (up - um) / (2.0 * P.h) : kNaN;
+    P.pp_u[item] = u0;
+    P.pp_d[item] = d;
+    P.pp_steps[item] = steps;
+    const bool bad = !isfinite(u0) || (P.crn && !isfinite(d));
+    if (bad) atomicOr(P.status, 1 << MCG_ERR_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// Plain double-precision walk.
+// ---------------------------------------------------------------------------
+template <bool CRN>
+__global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
+{
+    constexpr int NC = CRN ? 3 : 1;
+    bool busy = false, exhausted = false;
+    unsigned long long item = 0ull;
+    uint32_t s = 0u, p = 0u;
+    int64_t n = 0;
+    double W[3], I[NC], rp[NC], u[3];
+    unsigned alive = 0u;
+    int64_t steps = 0;
+    const double off[3] = {0.0, P.h, -P.h};
+    unsigned iter = 0u;
+
+    for (;;) {
+        if ((++iter & 255u) == 0u && cancelled(P)) {
+            if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
+            busy = false;
+            exhausted = true;
+        }
+        if (refill(P, busy, exhausted, item) &&
+            station_ok(P, s = (uint32_t)(item / (unsigned long long)P.N), item)) {
+            p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
+            for (int k = 0; k < 3; ++k) W[k] = P.stations[3 * s + k];
+            for (int c = 0; c < NC; ++c) {
+                const double X[3] = {W[0], W[1], __dadd_rn(W[2], off[c])};
+                rp[c] = rho_f64(P, X);
+                I[c] = 0.0;
+            }
+            u[0] = u[1] = u[2] = kNaN;
+            alive = (1u << NC) - 1u;
+            n = 0;
+            steps = 0;
+            busy = true;
+        }
+        if (!__any_sync(kFull, busy)) break;
+        if (!busy) continue;
+
+        double z[12];
+        normals12_f64(s, p, (uint32_t)(n >> 2), P.key0, P.key1, z);
+#pragma unroll 1
+        for (int m = 0; m < 4 && alive; ++m) {
+            const double dW[3] = {__dmul_rn(P.sd, z[3 * m]), __dmul_rn(P.sd, z[3 * m + 1]),
+                                  __dmul_rn(P.sd, z[3 * m + 2])};
+            const double Wn[3] = {__dadd_rn(W[0], dW[0]), __dadd_rn(W[1], dW[1]), __dadd_rn(W[2], dW[2])};
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (!(alive & (1u << c))) continue;
+                const double X[3] = {W[0], W[1], __dadd_rn(W[2], off[c])};
+                const double Y[3] = {Wn[0], Wn[1], __dadd_rn(Wn[2], off[c])};
+                steps += 1;
+                const bool inside = Y[0] > P.lo[0] && Y[0] < P.hi[0] && Y[1] > P.lo[1] && Y[1] < P.hi[1] &&
+                                    Y[2] > P.lo[2] && Y[2] < P.hi[2];
+                if (inside) {
+                    const double r = rho_f64(P, Y);
+                    I[c] = __dadd_rn(I[c], __dmul_rn(__dmul_rn(0.5, __dadd_rn(rp[c], r)), P.dt));
+                    rp[c] = r;
+                } else {
+                    u[c] = exit_fp64(P, X, dW, Y, I[c], rp[c]);
+                    alive &= ~(1u << c);
+                }
+            }
+            W[0] = Wn[0];
+            W[1] = Wn[1];
+            W[2] = Wn[2];
+            ++n;
+        }
+        if (!alive) {
+            write_path(P, item, u[0], u[1], u[2], steps);
+            busy = false;
+        } else if (n >= P.max_steps) {
+            atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
+            P.pp_u[item] = kNaN;
+            P.pp_d[item] = kNaN;
+            P.pp_steps[item] = steps;
+            busy = false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision walk.
+// ---------------------------------------------------------------------------
+template <int RHO, bool CRN>
+__global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
+{
+    bool busy = false, exhausted = false;
+    unsigned long long item = 0ull;
+    uint32_t s = 0u, p = 0u, blk = 0u;
+    float wx = 0.f, wy = 0.f, wz = 0.f;
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;   // single-precision partial sums
+    double D0 = 0.0, D1 = 0.0, D2 = 0.0;  // flushed sums
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // rho at the previous point
+    double u0 = kNaN, u1 = kNaN, u2 = kNaN;
+    unsigned alive = 0u;
+    int64_t steps = 0;
+    const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2];
+    const float hf = P.h_f;
+    unsigned iter = 0u;
+
+    for (;;) {
+        if ((++iter & 255u) == 0u && cancelled(P)) {
+            if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
+            busy = false;
+            exhausted = true;
+        }
+        if (refill(P, busy, exhausted, item) &&
+            station_ok(P, s = (uint32_t)(item / (unsigned long long)P.N), item)) {
+            p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
+            wx = (float)(P.stations[3 * s + 0] - P.cen[0]);
+            wy = (float)(P.stations[3 * s + 1] - P.cen[1]);
+            wz = (float)(P.stations[3 * s + 2] - P.cen[2]);
+            r0 = rho_f32<RHO>(P, wx, wy, wz);
+            S0 = 0.5f * r0;
+            D0 = 0.0;
+            if (CRN) {
+                r1 = rho_f32<RHO>(P, wx, wy, wz + hf);
+                r2 = rho_f32<RHO>(P, wx, wy, wz - hf);
+                S1 = 0.5f * r1;
+                S2 = 0.5f * r2;
+                D1 = D2 = 0.0;
+            }
+            u0 = u1 = u2 = kNaN;
+            alive = CRN ? 7u : 1u;
+            blk = 0u;
+            steps = 0;
+            busy = true;
+        }
+        if (!__any_sync(kFull, busy)) break;
+        if (!busy) continue;
+
+        float z[12];
+        normals12_f32(s, p, blk, P.key0, P.key1, P.lnscale_f, z);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float nx = wx + z[3 * m], ny = wy + z[3 * m + 1], nz = wz + z[3 * m + 2];
+            const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
+            const int64_t nstep = 4 * (int64_t)blk + m + 1;
+            if (alive & 1u) {
+                if (inxy && fabsf(nz) < hz) {
+                    r0 = rho_f32<RHO>(P, nx, ny, nz);
+                    S0 += r0;
+                } else {
+                    u0 = exit_mixed(P, wx, wy, wz, nx, ny, nz, D0 + (double)S0, r0);
+                    alive &= ~1u;
+                    steps += nstep;
+                }
+            }
+            if (CRN) {
+                if (alive & 2u) {
+                    const float zc = nz + hf;
+                    if (inxy && fabsf(zc) < hz) {
+                        r1 = rho_f32<RHO>(P, nx, ny, zc);
+                        S1 += r1;
+                    } else {
+                        u1 = exit_mixed(P, wx, wy, wz + hf, nx, ny, zc, D1 + (double)S1, r1);
+                        alive &= ~2u;
+                        steps += nstep;
+                    }
+                }
+                if (alive & 4u) {
+                    const float zc = nz - hf;
+                    if (inxy && fabsf(zc) < hz) {
+                        r2 = rho_f32<RHO>(P, nx, ny, zc);
+                        S2 += r2;
+                    } else {
+                        u2 = exit_mixed(P, wx, wy, wz - hf, nx, ny, zc, D2 + (double)S2, r2);
+                        alive &= ~4u;
+                        steps += nstep;
+                    }
+                }
+            }
+            wx = nx;
+            wy = ny;
+            wz = nz;
+            if (!alive) break;
+        }
+        ++blk;
+        if ((blk & 15u) == 0u) {  // flush every 64 steps
+            D0 += (double)S0;
+            S0 = 0.f;
+            if (CRN) {
+                D1 += (double)S1;
+                D2 += (double)S2;
+                S1 = S2 = 0.f;
+            }
+        }
+        if (!alive) {
+            write_path(P, item, u0, u1, u2, steps);
+            busy = false;
+        } else if (4 * (int64_t)blk >= P.max_steps) {
+            atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
+            P.pp_u[item] = kNaN;
+            P.pp_d[item] = kNaN;
+            P.pp_steps[item] = steps;
+            busy = false;
+        }
+    }
+}
+
+template <int RHO, bool CRN>
+cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t st)
+{
+    walk_mixed_kernel<RHO, CRN><<<grid, block, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int RHO>
+const void* mixed_fn(bool crn)
+{
+    return crn ? (const void*)walk_mixed_kernel<RHO, true> : (const void*)walk_mixed_kernel<RHO, false>;
+}
+
+const void* kernel_fn(int precision, int rho_kind, bool crn)
+{
+    if (precision == MCG_FP64) return crn ? (const void*)walk_fp64_kernel<true> : (const void*)walk_fp64_kernel<false>;
+    switch (rho_kind) {
+    case MCG_RHO_SPHERE: return mixed_fn<MCG_RHO_SPHERE>(crn);
+    case MCG_RHO_PRISM: return mixed_fn<MCG_RHO_PRISM>(crn);
+    case MCG_RHO_VOXEL: return mixed_fn<MCG_RHO_VOXEL>(crn);
+    default: return mixed_fn<MCG_RHO_NONE>(crn);
+    }
+}
+
+}  // namespace
+
+int walk_blocks_per_sm(int precision, int rho_kind, int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_fn(precision, rho_kind, true), block, 0) !=
+        cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = walk_blocks_per_sm(precision, P.rho_kind, block);
+    long long grid = (long long)sms * per_sm;
+    const long long need = (long long)((P.total + (unsigned long long)block - 1ull) / (unsigned long long)block);
+    if (grid > need) grid = need > 0 ? need : 1;
+    const bool crn = P.crn != 0;
+    if (precision == MCG_FP64) {
+        if (crn) walk_fp64_kernel<true><<<(int)grid, block, 0, st>>>(P);
+        else walk_fp64_kernel<false><<<(int)grid, block, 0, st>>>(P);
+        return cudaGetLastError();
+    }
+    switch (P.rho_kind) {
+    case MCG_RHO_SPHERE:
+        return crn ? launch_mixed<MCG_RHO_SPHERE, true>(P, block, (int)grid, st)
+                   : launch_mixed<MCG_RHO_SPHERE, false>(P, block, (int)grid, st);
+    case MCG_RHO_PRISM:
+        return crn ? launch_mixed<MCG_RHO_PRISM, true>(P, block, (int)grid, st)
+                   : launch_mixed<MCG_RHO_PRISM, false>(P, block, (int)grid, st);
+    case MCG_RHO_VOXEL:
+        return crn ? launch_mixed<MCG_RHO_VOXEL, true>(P, block, (int)grid, st)
+                   : launch_mixed<MCG_RHO_VOXEL, false>(P, block, (int)grid, st);
+    default:
+        return crn ? launch_mixed<MCG_RHO_NONE, true>(P, block, (int)grid, st)
+                   : launch_mixed<MCG_RHO_NONE, false>(P, block, (int)grid, st);
+    }
+}
+
+}  // namespace mcg

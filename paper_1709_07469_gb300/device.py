@@ -1,0 +1,82 @@
+"""Device-resident solve through the C ABI (torch provides memory and streams).
+
+``DeviceSolve`` owns the per-path buffers of one launch (S stations x N paths),
+the running station states and the status / work-counter words, and calls
+mcg_walk -> mcg_reduce -> mcg_finalize.  Nothing here computes: it allocates,
+passes pointers, and reads results back.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import mcgrav as M
+
+
+class DeviceSolve:
+    def __init__(self, w, stations=None, batch: int | None = None, precision: int = M.MCG_MIXED,
+                 grid=None, faces=None, device: str = "cuda", stream=None, block: int = 0):
+        self.w = w
+        self.dev = torch.device(device)
+        st = np.asarray(w.stations if stations is None else stations, dtype=np.float64).reshape(-1, 3)
+        self.S = st.shape[0]
+        self.stations = torch.from_numpy(st).to(self.dev)
+        self.batch = int(batch or w.paths)
+        self.precision = precision
+        self.stream = stream
+        self.prob = M.problem(w, grid=grid, faces=faces)
+        self.opts = M.options(w, precision=precision, stream=stream, block=block)
+        n = self.S * self.batch
+        self.pp_u = torch.empty(n, dtype=torch.float64, device=self.dev)
+        self.pp_d = torch.empty(n, dtype=torch.float64, device=self.dev)
+        self.pp_steps = torch.empty(n, dtype=torch.int64, device=self.dev)
+        self.states = torch.zeros(self.S * M.STATE_BYTES // 8, dtype=torch.float64, device=self.dev)
+        self.status = torch.zeros(2, dtype=torch.int32, device=self.dev)
+        self.counter = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        self.res = torch.empty((6, self.S), dtype=torch.float64, device=self.dev)
+
+    def reset(self):
+        self.states.zero_()
+        self.status.zero_()
+
+    def walk(self, p0: int, N: int | None = None):
+        """Launch the walk for paths p0 .. p0+N-1 of every station."""
+        N = self.batch if N is None else N
+        M.mcg_walk(self.prob, self.stations, self.S, p0, N, self.w.dt, self.w.seed, self.opts,
+                   self.pp_u, self.pp_d, self.pp_steps, self.status, self.counter)
+        return N
+
+    def reduce(self, N: int | None = None):
+        N = self.batch if N is None else N
+        M.mcg_reduce(self.pp_u, self.pp_d, self.pp_steps, self.S, N, self.states, self.stream)
+
+    def finalize(self):
+        r = self.res
+        M.mcg_finalize(self.states, self.S, r[0], r[1], r[2], r[3], r[4], r[5], self.stream)
+
+    def run(self, paths: int | None = None, p0: int = 0):
+        """Whole solve over paths p0 .. p0+paths-1 in batches; returns host dict."""
+        paths = self.w.paths if paths is None else paths
+        self.reset()
+        done = 0
+        while done < paths:
+            nb = min(self.batch, paths - done)
+            self.walk(p0 + done, nb)
+            self.reduce(nb)
+            done += nb
+        self.finalize()
+        return self.result()
+
+    def result(self):
+        torch.cuda.synchronize(self.dev)
+        r = self.res.cpu().numpy()
+        return {"u": r[0].copy(), "gz": r[1].copy(), "se_u": r[2].copy(), "se_gz": r[3].copy(),
+                "n_paths": r[4].view(np.int64).copy(), "path_steps": r[5].view(np.int64).copy(),
+                "status": int(self.status[0].item())}
+
+    def per_path(self, N: int | None = None):
+        N = self.batch if N is None else N
+        torch.cuda.synchronize(self.dev)
+        k = self.S * N
+        return (self.pp_u[:k].cpu().numpy().reshape(self.S, N), self.pp_d[:k].cpu().numpy().reshape(self.S, N),
+                self.pp_steps[:k].cpu().numpy().reshape(self.S, N))

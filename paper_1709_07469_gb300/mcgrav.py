@@ -1,0 +1,254 @@
+"""ctypes binding of libmcgrav (include/mcgrav.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts numpy
+arrays / torch tensors into the C structures and pointers and turns status
+codes into exceptions.  Loading fails loudly if the library has not been
+built (``python -m paper_1709_07469_gb300.build``): there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MCG_OK, MCG_ERR_ARG, MCG_ERR_OOM, MCG_ERR_CUDA = 0, 1, 2, 3
+MCG_ERR_STEP_CAP, MCG_ERR_TIMEOUT, MCG_ERR_NONFINITE, MCG_ERR_CANCELLED = 4, 5, 6, 7
+MCG_RHO_NONE, MCG_RHO_SPHERE, MCG_RHO_PRISM, MCG_RHO_VOXEL = 0, 1, 2, 3
+MCG_G_ZERO, MCG_G_SPHERE, MCG_G_PRISM, MCG_G_TABLE, MCG_G_POLY = 0, 1, 2, 3, 4
+MCG_FP64, MCG_MIXED = 0, 1
+
+_RHO = {"none": MCG_RHO_NONE, "sphere": MCG_RHO_SPHERE, "prism": MCG_RHO_PRISM, "voxel": MCG_RHO_VOXEL}
+_G = {"zero": MCG_G_ZERO, "sphere": MCG_G_SPHERE, "prism": MCG_G_PRISM, "table": MCG_G_TABLE, "poly": MCG_G_POLY}
+
+D3 = C.c_double * 3
+
+
+class mcg_domain(C.Structure):
+    _fields_ = [("lo", D3), ("hi", D3)]
+
+
+class mcg_density(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("G", C.c_double), ("rho0", C.c_double), ("center", D3),
+                ("radius", C.c_double), ("lo", D3), ("hi", D3), ("grid", C.c_void_p),
+                ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("origin", D3), ("spacing", D3)]
+
+
+class mcg_boundary(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("faces", C.c_void_p), ("nu", C.c_int32), ("nv", C.c_int32),
+                ("poly", C.c_double * 11)]
+
+
+class mcg_options(C.Structure):
+    _fields_ = [("h", C.c_double), ("sigma", C.c_double), ("precision", C.c_int32), ("clip", C.c_int32),
+                ("crn_gz", C.c_int32), ("block", C.c_int32), ("max_steps", C.c_int64),
+                ("batch_paths", C.c_int64), ("stream", C.c_void_p), ("cancel", C.c_void_p)]
+
+
+class mcg_result(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("gz", C.c_void_p), ("se_u", C.c_void_p), ("se_gz", C.c_void_p),
+                ("n_paths", C.c_void_p), ("path_steps", C.c_void_p)]
+
+
+class mcg_station_state(C.Structure):
+    _fields_ = [("n", C.c_double), ("mean_u", C.c_double), ("m2_u", C.c_double), ("mean_d", C.c_double),
+                ("m2_d", C.c_double), ("steps", C.c_double), ("pad", C.c_double * 2)]
+
+
+STATE_BYTES = C.sizeof(mcg_station_state)
+
+
+class McgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mcgrav status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libmcgrav.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise ImportError(f"libmcgrav.so not built at {p}; run paper_1709_07469_gb300.build.build()")
+    lib = C.CDLL(p)
+    vp, i32, i64, u32, u64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+    P = C.POINTER
+    lib.mcg_options_default.argtypes = [P(mcg_options)]
+    lib.mcg_options_default.restype = None
+    lib.mcg_last_error.restype = C.c_char_p
+    lib.mcg_version.restype = C.c_char_p
+    lib.mcgrav_solve.argtypes = [P(mcg_domain), P(mcg_density), P(mcg_boundary), vp, i64, i64, d, u64,
+                                 P(mcg_options), P(mcg_result)]
+    lib.mcgrav_solve.restype = C.c_int
+    lib.mcg_walk.argtypes = [P(mcg_domain), P(mcg_density), P(mcg_boundary), vp, i64, i64, i64, d, u64,
+                             P(mcg_options), vp, vp, vp, vp, vp]
+    lib.mcg_walk.restype = C.c_int
+    lib.mcg_reduce.argtypes = [vp, vp, vp, i64, i64, vp, vp]
+    lib.mcg_reduce.restype = C.c_int
+    lib.mcg_finalize.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+    lib.mcg_finalize.restype = C.c_int
+    lib.mcg_workspace_bytes.argtypes = [i64, i64]
+    lib.mcg_workspace_bytes.restype = C.c_size_t
+    lib.mcg_philox.argtypes = [vp, vp, i64, vp, vp]
+    lib.mcg_philox.restype = C.c_int
+    lib.mcg_normals.argtypes = [u64, u32, u32, u32, i64, i32, vp, vp]
+    lib.mcg_normals.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, allow=()):
+    if rc != MCG_OK and rc not in allow:
+        raise McgError(rc, load().mcg_last_error().decode())
+    return rc
+
+
+def last_error() -> str:
+    return load().mcg_last_error().decode()
+
+
+def version() -> str:
+    return load().mcg_version().decode()
+
+
+def _ptr(x) -> int | None:
+    """Device pointer of a torch tensor, host pointer of a numpy array, or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# --- problem description ----------------------------------------------------
+
+@dataclass
+class Problem:
+    domain: mcg_domain
+    density: mcg_density
+    boundary: mcg_boundary
+    keep: tuple = ()
+
+
+def problem(w, grid=None, faces=None) -> Problem:
+    """C structures of a workload (paper_1709_07469_gb300.workloads.Workload).
+    `grid` / `faces` are device tensors (float32) when the workload uses them."""
+    dom = mcg_domain(D3(*w.lo), D3(*w.hi))
+    den = mcg_density()
+    den.kind = _RHO[w.rho_kind]
+    den.G, den.rho0 = w.G, w.rho0
+    den.center, den.radius = D3(*w.center), w.radius
+    if w.rho_kind == "prism":
+        den.lo, den.hi = D3(*w.plo), D3(*w.phi)
+    if w.rho_kind == "voxel":
+        if grid is None:
+            raise ValueError("voxel workload needs a device grid")
+        nz, ny, nx = grid.shape
+        den.grid = _ptr(grid)
+        den.nx, den.ny, den.nz = nx, ny, nz
+        den.origin, den.spacing = D3(*w.grid_origin), D3(*w.grid_spacing)
+    bnd = mcg_boundary()
+    bnd.kind = _G[w.g_kind]
+    bnd.poly = (C.c_double * 11)(*[float(c) for c in w.poly])
+    if w.g_kind == "table":
+        if faces is None:
+            raise ValueError("table workload needs device faces")
+        bnd.faces = _ptr(faces)
+        bnd.nv, bnd.nu = faces.shape[1], faces.shape[2]
+    return Problem(dom, den, bnd, (grid, faces))
+
+
+def options(w=None, precision: int = MCG_MIXED, stream=None, **kw) -> mcg_options:
+    o = mcg_options()
+    load().mcg_options_default(C.byref(o))
+    o.precision = precision
+    if w is not None:
+        o.h, o.sigma, o.clip, o.crn_gz = w.h, w.sigma, w.clip, w.crn
+    o.stream = _stream_handle(stream)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# --- entry points -------------------------------------------------------------
+
+@dataclass
+class SolveResult:
+    status: int
+    u: np.ndarray
+    gz: np.ndarray
+    se_u: np.ndarray
+    se_gz: np.ndarray
+    n_paths: np.ndarray
+    path_steps: np.ndarray
+
+
+def mcgrav_solve(prob: Problem, stations: np.ndarray, paths: int, dt: float, seed: int, opts: mcg_options,
+                 allow=()) -> SolveResult:
+    """Blocking one-call solve with HOST stations and HOST results."""
+    lib = load()
+    st = np.ascontiguousarray(stations, dtype=np.float64).reshape(-1, 3)
+    S = st.shape[0]
+    out = {k: np.full(S, np.nan) for k in ("u", "gz", "se_u", "se_gz")}
+    out["n_paths"] = np.zeros(S, dtype=np.int64)
+    out["path_steps"] = np.zeros(S, dtype=np.int64)
+    res = mcg_result(*[out[k].ctypes.data for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps")])
+    rc = lib.mcgrav_solve(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary), st.ctypes.data,
+                          S, paths, dt, seed & 0xFFFFFFFFFFFFFFFF, C.byref(opts), C.byref(res))
+    _check(rc, allow)
+    return SolveResult(rc, **out)
+
+
+def mcg_walk(prob: Problem, stations_dev, S: int, p0: int, N: int, dt: float, seed: int, opts: mcg_options,
+             pp_u, pp_d, pp_steps, status_dev, counter_dev) -> int:
+    """Asynchronous walk launch on device buffers (torch tensors)."""
+    rc = load().mcg_walk(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary), _ptr(stations_dev),
+                         S, p0, N, dt, seed & 0xFFFFFFFFFFFFFFFF, C.byref(opts), _ptr(pp_u), _ptr(pp_d),
+                         _ptr(pp_steps), _ptr(status_dev), _ptr(counter_dev))
+    return _check(rc)
+
+
+def mcg_reduce(pp_u, pp_d, pp_steps, S: int, N: int, states_dev, stream=None) -> int:
+    return _check(load().mcg_reduce(_ptr(pp_u), _ptr(pp_d), _ptr(pp_steps), S, N, _ptr(states_dev),
+                                    _stream_handle(stream)))
+
+
+def mcg_finalize(states_dev, S: int, u=None, gz=None, se_u=None, se_gz=None, n_paths=None, path_steps=None,
+                 stream=None) -> int:
+    return _check(load().mcg_finalize(_ptr(states_dev), S, _ptr(u), _ptr(gz), _ptr(se_u), _ptr(se_gz),
+                                      _ptr(n_paths), _ptr(path_steps), _stream_handle(stream)))
+
+
+def mcg_workspace_bytes(S: int, batch: int) -> int:
+    return int(load().mcg_workspace_bytes(S, batch))
+
+
+def mcg_philox(ctr_dev, key_dev, n: int, out_dev, stream=None) -> int:
+    return _check(load().mcg_philox(_ptr(ctr_dev), _ptr(key_dev), n, _ptr(out_dev), _stream_handle(stream)))
+
+
+def mcg_normals(seed: int, s: int, p: int, b0: int, nblocks: int, precision: int, out_dev, stream=None) -> int:
+    return _check(load().mcg_normals(seed & 0xFFFFFFFFFFFFFFFF, s, p, b0, nblocks, precision, _ptr(out_dev),
+                                     _stream_handle(stream)))

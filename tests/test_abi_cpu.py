@@ -1,0 +1,106 @@
+"""The C-ABI library builds, loads and exports every symbol include/mcgrav.h
+declares; the ctypes structures match the C layout; host-side argument checks
+answer without a GPU.  No compute call is made here."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1709_07469_gb300 import build as B
+from paper_1709_07469_gb300 import mcgrav as M
+from paper_1709_07469_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.load()
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        names += re.findall(r"^MCG_API\s+[\w\s\*]+?\b(mcg\w*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "mcgrav_solve" in names and "mcg_walk" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "layout.c"
+    structs = {"mcg_domain": M.mcg_domain, "mcg_density": M.mcg_density, "mcg_boundary": M.mcg_boundary,
+               "mcg_options": M.mcg_options, "mcg_result": M.mcg_result, "mcg_station_state": M.mcg_station_state}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcgrav.h"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def test_defaults_and_workspace(lib):
+    o = M.mcg_options()
+    lib.mcg_options_default(C.byref(o))
+    assert o.h == 1e-2 and o.sigma == 1.0 and o.precision == M.MCG_MIXED and o.clip == 1 and o.crn_gz == 1
+    assert o.max_steps == 1 << 31
+    assert M.mcg_workspace_bytes(0, 10) == 0
+    b = M.mcg_workspace_bytes(30, 1000)
+    assert b >= 30 * 1000 * 24 and b < 30 * 1000 * 24 + 64 * 1024
+    assert "sm_103a" in M.version()
+
+
+def _solve_status(w, **kw):
+    prob = M.problem(w)
+    opts = M.options(w, **kw)
+    lib = M.load()
+    st = np.ascontiguousarray(w.stations, dtype=np.float64)
+    res = M.mcg_result()
+    return lib.mcgrav_solve(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary), st.ctypes.data,
+                            st.shape[0], w.paths, w.dt, 0, C.byref(opts), C.byref(res))
+
+
+def test_argument_checks_without_gpu(lib):
+    w = W.sphere_line(paths=10)
+    assert _solve_status(w.with_(dt=-1.0)) == M.MCG_ERR_ARG
+    assert "dt" in M.last_error()
+    assert _solve_status(w.with_(stations=np.array([[0.0, 0.0, 1.0]]))) == M.MCG_ERR_ARG
+    assert "inside" in M.last_error()
+    assert _solve_status(w.with_(stations=np.array([[0.0, 0.0, 0.995]]))) == M.MCG_ERR_ARG  # +h copy outside
+    assert _solve_status(w.with_(lo=(1.0, -1.0, -1.0))) == M.MCG_ERR_ARG
+    assert _solve_status(w.with_(g_kind="prism")) == M.MCG_ERR_ARG
+    assert _solve_status(w, block=48) == M.MCG_ERR_ARG
+    assert _solve_status(w, precision=7) == M.MCG_ERR_ARG
+    assert _solve_status(w.with_(paths=0)) == M.MCG_ERR_ARG
+    # empty station list is a no-op
+    assert _solve_status(w.with_(stations=np.zeros((0, 3)))) == M.MCG_OK
+
+
+def test_product_path_fails_loudly_without_library(tmp_path):
+    saved = M._lib
+    try:
+        M._lib = None
+        with pytest.raises(ImportError):
+            M.load(str(tmp_path / "missing.so"))
+    finally:
+        M._lib = saved

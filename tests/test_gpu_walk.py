@@ -1,0 +1,223 @@
+"""GPU walk against the oracle, through the C ABI (the parity gate).
+
+Tolerances:
+* plain FP64 walk, per path: the two sides run the same operation sequence
+  and differ only in the last bits of log / sin / cos, so where the exit step
+  matches, |du| <= 1e-12 |u| and |dd| <= 1e-12 |u| / h (the centred
+  difference divides by 2h); the fraction of paths whose exit step flips
+  must stay below 1e-4;
+* mixed walk, per path, against the oracle run on the same 23-bit uniforms:
+  most paths agree to single-precision rounding; the paired mean difference
+  must be within 4 standard errors of the differences plus the shift that
+  single-precision inputs alone cause (station coordinates and step scale
+  rounded to 2^-24 relative move u by ~1e-8 relative; allowance 1e-6 |u|,
+  and 1e-6 |u| / h for the centred difference);
+* station statistics: within 4 standard errors of the closed form where the
+  estimator is exactly unbiased.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_07469_gb300 import build as B
+from paper_1709_07469_gb300 import mcgrav as M
+from paper_1709_07469_gb300 import workloads as W
+from paper_1709_07469_gb300.device import DeviceSolve
+from tests.helpers import oracle_spec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    B.build()
+    M.load()
+
+
+def gpu_per_path(w, precision, paths=None, stations=None, p0=0, **kw):
+    ds = DeviceSolve(w, stations=stations, batch=paths or w.paths, precision=precision, **kw)
+    ds.reset()
+    ds.walk(p0)
+    u, d, st = ds.per_path()
+    return u, d, st, int(ds.status[0].item())
+
+
+def compare_fp64(w, paths, stations=None, p0=0):
+    u, d, st, status = gpu_per_path(w, M.MCG_FP64, paths, stations, p0)
+    assert status == 0
+    S = u.shape[0]
+    ref = oracle.solve(oracle_spec(w), w.stations if stations is None else stations, paths, p0=p0, per_path=True)
+    same = st == ref.pp_steps
+    flips = 1.0 - same.mean()
+    tol_u = 1e-12 * np.abs(ref.pp_u)
+    tol_d = 1e-12 * np.abs(ref.pp_u) / w.h + 1e-300
+    assert np.all(np.abs(u - ref.pp_u)[same] <= tol_u[same])
+    assert np.all(np.abs(d - ref.pp_d)[same] <= tol_d[same])
+    return flips, S * paths
+
+
+def test_fp64_per_path_sphere_line_full():
+    """Sphere workload, all 8 stations x 2e4 paths (the full configuration)."""
+    w = W.sphere_line()
+    flips, n = compare_fp64(w, w.paths)
+    assert flips < 1e-4, flips
+
+
+def test_fp64_per_path_prism_sampled_paths():
+    """Prism ore body (step 1 m, ~1e5 steps per path): a sample of paths at
+    high path indices, as in the full 10^6-path launch."""
+    w = W.prism_ore_body()
+    st = w.stations[[0, 7, 14, 22]]
+    flips, n = compare_fp64(w.with_(stations=st), 6, p0=999_990)
+    assert flips <= 1.0 / n + 1e-12
+
+
+@pytest.mark.parametrize("name,poly", [("linear", (0.3, 1.0, 2.0, -1.0, 0, 0, 0, 0, 0, 0, 0)),
+                                       ("xyz", (0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3.0))])
+def test_fp64_per_path_harmonic_ragged(name, poly):
+    """clip = 0 and crn on, a ragged path count (not a multiple of 32)."""
+    st = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.5], [0.8, 0.7, -0.6]])
+    w = W.unit_box(st, g_kind="poly", poly=poly, dt=0.02, paths=1001, clip=0, h=0.05)
+    flips, n = compare_fp64(w, w.paths)
+    assert flips < 1e-3
+
+
+def test_mixed_vs_oracle_paired_sphere_line():
+    w = W.sphere_line(paths=20000)
+    u, d, st, status = gpu_per_path(w, M.MCG_MIXED)
+    assert status == 0
+    ref = oracle.solve(oracle_spec(w, ubits=23), w.stations, w.paths, per_path=True)
+    same = st == ref.pp_steps
+    assert same.mean() > 0.97, same.mean()
+    rel = np.abs(u - ref.pp_u)[same] / np.abs(ref.pp_u)[same]
+    assert np.quantile(rel, 0.99) < 1e-4
+    for s in range(w.n_stations):
+        diff = u[s] - ref.pp_u[s]
+        se = diff.std(ddof=1) / math.sqrt(diff.size)
+        um = abs(ref.pp_u[s].mean())
+        assert abs(diff.mean()) <= 4 * se + 1e-6 * um, (s, diff.mean(), se)
+        dd = d[s] - ref.pp_d[s]
+        se_d = dd.std(ddof=1) / math.sqrt(dd.size)
+        assert abs(dd.mean()) <= 4 * se_d + 1e-6 * um / w.h, (s, dd.mean(), se_d)
+        # the shift is below a thousandth of the estimate's own standard error
+        assert abs(diff.mean()) < 1e-3 * ref.pp_u[s].std(ddof=1) / math.sqrt(diff.size)
+
+
+@pytest.mark.parametrize("precision", [M.MCG_FP64, M.MCG_MIXED])
+def test_sphere_line_vs_closed_form(precision):
+    w = W.sphere_line()
+    r = DeviceSolve(w, precision=precision).run()
+    assert r["status"] == 0
+    Mass = 4 / 3 * math.pi * 0.25**3
+    z = w.stations[:, 2]
+    assert np.all(np.abs(r["u"] + Mass / z) < 4 * r["se_u"] + 2e-4), (r["u"] + Mass / z) / r["se_u"]
+    assert np.all(np.abs(r["gz"] - Mass / z**2) < 4 * r["se_gz"])
+    assert np.all(r["n_paths"] == w.paths)
+
+
+@pytest.mark.parametrize("precision", [M.MCG_FP64, M.MCG_MIXED])
+def test_station_statistics_match_oracle(precision):
+    """Means, standard errors and step totals against the oracle's two-pass
+    statistics on the same paths (FP64: 1e-12; mixed: within 4 SE)."""
+    w = W.sphere_line(paths=5000)
+    r = DeviceSolve(w, precision=precision, batch=1237).run()   # ragged batches
+    ref = oracle.solve(oracle_spec(w, ubits=32 if precision == M.MCG_FP64 else 23), w.stations, w.paths)
+    if precision == M.MCG_FP64:
+        np.testing.assert_allclose(r["u"], ref.u, rtol=1e-11)
+        np.testing.assert_allclose(r["se_u"], ref.se_u, rtol=1e-9)
+        np.testing.assert_allclose(r["gz"], ref.gz, rtol=1e-9)
+        assert np.array_equal(r["path_steps"], ref.path_steps)
+    else:
+        assert np.all(np.abs(r["u"] - ref.u) < 4 * ref.se_u)
+        assert np.all(np.abs(r["gz"] - ref.gz) < 4 * ref.se_gz)
+        np.testing.assert_allclose(r["se_u"], ref.se_u, rtol=0.05)
+
+
+HARMONIC = [(0.3, 1.0, 2.0, -1.0, 0, 0, 0, 0, 0, 0, 0), (0, 0, 0, 0, 1.0, -1.0, 0, 0, 0, 0, 0),
+            (0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3.0), (0, 0, 0, 0, 1.0, 1.0, -2.0, 0, 0, 0, 0)]
+
+
+def poly_eval(c, x):
+    X, Y, Z = x
+    return (c[0] + c[1] * X + c[2] * Y + c[3] * Z + c[4] * X * X + c[5] * Y * Y + c[6] * Z * Z
+            + c[7] * X * Y + c[8] * Y * Z + c[9] * Z * X + c[10] * X * Y * Z)
+
+
+@pytest.mark.parametrize("precision", [M.MCG_FP64, M.MCG_MIXED])
+@pytest.mark.parametrize("k", range(4))
+def test_harmonic_unbiased_gpu(precision, k):
+    st = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.5], [0.8, 0.7, -0.6], [-0.9, 0.1, 0.85]])
+    w = W.unit_box(st, g_kind="poly", poly=HARMONIC[k], dt=0.01, paths=200_000, clip=0, h=0.05)
+    r = DeviceSolve(w, precision=precision).run()
+    assert r["status"] == 0
+    for s, x in enumerate(st):
+        assert abs(r["u"][s] - poly_eval(HARMONIC[k], x)) < 4 * r["se_u"][s] + 1e-12
+        want_d = (poly_eval(HARMONIC[k], x + [0, 0, w.h]) - poly_eval(HARMONIC[k], x - [0, 0, w.h])) / (2 * w.h)
+        assert abs(r["gz"][s] - want_d) < 4 * r["se_gz"][s] + 1e-12
+
+
+@pytest.mark.parametrize("precision", [M.MCG_FP64, M.MCG_MIXED])
+def test_constant_density_quadratic_gpu(precision):
+    A = 2 * math.pi / 3
+    st = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.5], [0.8, 0.7, -0.6]])
+    w = W.unit_box(st, rho_kind="prism", rho0=1.0, g_kind="poly", poly=(0, 0, 0, 0, A, A, A, 0, 0, 0, 0),
+                   dt=0.01, paths=200_000, clip=0, h=0.05)
+    r = DeviceSolve(w, precision=precision).run()
+    for s, x in enumerate(st):
+        assert abs(r["u"][s] - A * np.dot(x, x)) < 4 * r["se_u"][s]
+        assert abs(r["gz"][s] - 2 * A * x[2]) < 4 * r["se_gz"][s] + 1e-12
+
+
+def test_mcgrav_solve_matches_device_path_and_is_deterministic():
+    w = W.sphere_line(paths=3000)
+    prob = M.problem(w)
+    a = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=3000))
+    b = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=3000))
+    c = DeviceSolve(w, precision=M.MCG_MIXED).run()
+    for k in ("u", "gz", "se_u", "se_gz"):
+        assert np.array_equal(getattr(a, k), getattr(b, k))
+        assert np.array_equal(getattr(a, k), c[k])
+    assert np.array_equal(a.path_steps, c["path_steps"])
+    # batching changes only the merge order of the statistics
+    d = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=777))
+    np.testing.assert_allclose(d.u, a.u, rtol=1e-12)
+    assert np.array_equal(d.path_steps, a.path_steps)
+
+
+def test_per_path_values_independent_of_launch_shape():
+    w = W.sphere_line(paths=2000)
+    u1, d1, s1, _ = gpu_per_path(w, M.MCG_MIXED, block=128)
+    u2, d2, s2, _ = gpu_per_path(w, M.MCG_MIXED, block=32)
+    assert np.array_equal(u1, u2) and np.array_equal(d1, d2) and np.array_equal(s1, s2)
+
+
+def test_edge_cases():
+    w = W.sphere_line(paths=1)
+    r = M.mcgrav_solve(M.problem(w), w.stations[:1], 1, w.dt, w.seed, M.options(w))
+    assert r.n_paths[0] == 1 and math.isnan(r.se_u[0])
+    r = M.mcgrav_solve(M.problem(w), np.zeros((0, 3)), 5, w.dt, w.seed, M.options(w))
+    assert r.u.size == 0
+    # step cap: every path stopped early -> status and NaN
+    w = W.sphere_line(paths=64)
+    r = M.mcgrav_solve(M.problem(w), w.stations, 64, w.dt, w.seed, M.options(w, max_steps=8),
+                       allow=(M.MCG_ERR_STEP_CAP,))
+    assert r.status == M.MCG_ERR_STEP_CAP and np.all(np.isnan(r.u))
+    # no common random numbers: g_z is NaN, u unchanged vs the crn run
+    a = M.mcgrav_solve(M.problem(w), w.stations, 64, w.dt, w.seed, M.options(w))
+    b = M.mcgrav_solve(M.problem(w), w.stations, 64, w.dt, w.seed, M.options(w, crn_gz=0))
+    assert np.all(np.isnan(b.gz)) and np.array_equal(a.u, b.u)
+
+
+def test_device_station_outside_flags_status():
+    w = W.sphere_line(paths=32)
+    st = w.stations.copy()
+    st[3] = [0.0, 0.0, 1.5]
+    ds = DeviceSolve(w, stations=st, precision=M.MCG_MIXED)
+    ds.reset()
+    ds.walk(0)
+    u, d, s, status = *ds.per_path(), int(ds.status[0].item())
+    assert status & (1 << M.MCG_ERR_ARG)
+    assert np.all(np.isnan(u[3])) and np.all(np.isfinite(u[[0, 1, 2, 4, 5, 6, 7]]))
