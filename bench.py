@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark: Feynman-Kac gravity walk on the prism ore-body workload.
+
+Workload (one GPU): prism ore body, 30 stations (5 x 3 grid at z = 0 and
+z = +50 m) over a 200 x 200 x 100 m prism (500 kg/m^3, top 150 m deep) in
+[-1000,1000]^2 x [-1000,200] m, analytic prism potential as Dirichlet data,
+step length 1 m, h = 1 m, 10^6 paths per station in total.
+
+A step is one pass of the whole hot path over one batch: the walk of B paths
+for each of the 30 stations (RNG, Euler-Maruyama, density, trapezoid, exit
+clip, boundary value, per-path estimates), the station reduction into the
+running statistics and the finalize.  Consecutive steps take consecutive path
+ranges and alternate between two CUDA streams so that one batch's exit-time
+tail overlaps the next batch; reductions are chained by events so the merge
+order stays fixed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the plain CPU
+oracle on the same workload instead (bounded per-step sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "path-steps/s & stations/s at 1e-3 rel std err, mixed vs FP64 walk; p50/p99 ms"
+UNIT = "path-steps/s"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# Ideal lane-instruction count per path-step of the mixed walk (model in the design doc).
+OPS_PER_PATH_STEP = 29.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32768, help="paths per station per step")
+    ap.add_argument("--cpu-paths", type=int, default=48, help="paths per station in the CPU-oracle sample")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--capped-only", action="store_true",
+                    help="only the tail-free stepping-rate launches (small profiling case)")
+    return ap.parse_args()
+
+
+# --- clocks -----------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, dev_index: int = 0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != dev_index:
+                    continue
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --- distributed --------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def allreduce(vals, op, world):
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=op)
+    return t.tolist()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --- CPU oracle -----------------------------------------------------------------
+
+def cpu_oracle_rate(w, paths, p0=0):
+    import oracle
+    from tests.helpers import oracle_spec
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.solve(oracle_spec(w, ubits=32), w.stations, paths, p0=p0, threads=threads)
+    dt = time.perf_counter() - t0
+    return float(r.path_steps.sum()) / dt, dt, threads, r
+
+
+# --- reference arm: the oracle ----------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1709_07469_gb300 import workloads as W
+    w = W.prism_ore_body()
+    lat, steps_total, t_total = [], 0.0, 0.0
+    cores = os.cpu_count() or 1
+    for k in range(args.warmup + args.steps):
+        rate, dt, cores, r = cpu_oracle_rate(w, args.cpu_paths, p0=k * args.cpu_paths)
+        if k >= args.warmup:
+            lat.append(dt * 1e3)
+            steps_total += float(r.path_steps.sum())
+            t_total += dt
+    value = steps_total / t_total
+    sample = f"{w.n_stations} stations x {args.cpu_paths} paths per step (FP64 oracle, OpenMP)"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "prism_ore_body", "stations": w.n_stations, "paths_per_station_per_step":
+                       args.cpu_paths, "step_m": 1.0, "parallelism": f"{cores} host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --- our arm ------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_1709_07469_gb300 import build as B
+    from paper_1709_07469_gb300 import mcgrav as M
+    from paper_1709_07469_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    M.load()
+    dev = torch.device("cuda", local)
+
+    w = W.prism_ore_body()
+    S, Bp = w.n_stations, args.batch
+    total_paths = w.paths
+    prob = M.problem(w)
+    stations = torch.from_numpy(np.ascontiguousarray(w.stations)).to(dev)
+    streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    bufs = []
+    for _ in range(2):
+        bufs.append({"u": torch.empty(S * Bp, dtype=torch.float64, device=dev),
+                     "d": torch.empty(S * Bp, dtype=torch.float64, device=dev),
+                     "st": torch.empty(S * Bp, dtype=torch.int64, device=dev),
+                     "ctr": torch.zeros(1, dtype=torch.int64, device=dev),
+                     "work": torch.empty(M.mcg_walk_work_bytes(S, Bp, M.MCG_MIXED), dtype=torch.uint8, device=dev)})
+    states = torch.zeros(S * M.STATE_BYTES // 8, dtype=torch.float64, device=dev)
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    res = torch.empty((6, S), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    opts = [M.options(w, precision=M.MCG_MIXED, stream=s) for s in streams]
+
+    def path_block(j):
+        # step j of this rank takes paths [p0, p0 + Bp) of every station (wrapping)
+        return ((j * world + rank) * Bp) % total_paths
+
+    n_steps = args.warmup + args.steps
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)] for k in
+          ("start", "walk0", "walk1", "end")}
+
+    def issue(j):
+        s = streams[j % 2]
+        b = bufs[j % 2]
+        with torch.cuda.stream(s):
+            ev["start"][j].record(s)
+            flush.zero_()
+            ev["walk0"][j].record(s)
+            M.mcg_walk(prob, stations, S, path_block(j), Bp, w.dt, w.seed, opts[j % 2], b["u"], b["d"], b["st"],
+                       b["work"], status, b["ctr"])
+            ev["walk1"][j].record(s)
+            if j > 0:
+                s.wait_event(ev["end"][j - 1])
+            M.mcg_reduce(b["u"], b["d"], b["st"], S, Bp, states, s)
+            M.mcg_finalize(states, S, res[0], res[1], res[2], res[3], res[4], res[5], s)
+            ev["end"][j].record(s)
+
+    for j in range(args.warmup):
+        issue(j)
+    torch.cuda.synchronize(dev)
+    states.zero_()
+    status.zero_()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = ClockSampler()
+    clk.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(streams[0])
+    streams[1].wait_event(t_start)
+    for j in range(args.warmup, n_steps):
+        issue(j)
+    streams[0].wait_event(ev["end"][n_steps - 1])
+    t_end.record(streams[0])
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = clk.stop(0)
+    elapsed_ms = t_start.elapsed_time(t_end)
+
+    r = res.cpu().numpy()
+    path_steps_local = float(r[5].view(np.int64).sum())
+    st_code = int(status[0].item())
+    walk_ms = [ev["walk0"][j].elapsed_time(ev["walk1"][j]) for j in range(args.warmup, n_steps)]
+    lat_ms = [ev["start"][j].elapsed_time(ev["end"][j]) for j in range(args.warmup, n_steps)]
+    max_ms, = allreduce([elapsed_ms], _max_op(world), world)
+    total_steps, = allreduce([path_steps_local], _sum_op(world), world)
+    value = total_steps / (max_ms / 1e3)
+
+    # stations/s at 1e-3 relative standard error (Sec. 2.3 error discussion):
+    # per-station paths needed N_req = (s_u / (1e-3 |u|))^2 from the measured
+    # per-path standard deviation s_u = se_u sqrt(n).
+    u, se_u, n_paths = r[0], r[2], r[4].view(np.int64).astype(np.float64)
+    s_u = se_u * np.sqrt(n_paths)
+    n_req = np.ceil((s_u / (1e-3 * np.abs(u))) ** 2)
+    paths_per_s = (S * Bp * args.steps * world) / (max_ms / 1e3)
+    stations_per_s = paths_per_s / float(np.mean(n_req))
+    mean_steps_per_path = path_steps_local / (S * Bp * args.steps)
+
+    out = {}
+    if rank == 0:
+        # roofline of the dominant kernel (the mixed walk): model lane-instructions
+        # per launch / average walk-kernel duration, against one warp-instruction
+        # per clock per scheduler at the maximum SM clock
+        per_launch_ops = OPS_PER_PATH_STEP * path_steps_local / args.steps
+        avg_walk_s = statistics.mean(walk_ms) / 1e3
+        achieved = per_launch_ops / avg_walk_s / 1e12
+        peak = SM_COUNT * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+                           "frac": achieved / peak, "traffic": None,
+                           "kernel": "walk_mixed_kernel<PRISM,crn>",
+                           "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (recipe unit counts)"}
+        if not args.skip_fp64:
+            out["fp64_walk"] = fp64_comparison(M, w, dev)
+        if not args.skip_e2e:
+            out["e2e"] = e2e_solve(M, w, Bp, max(1, min(args.steps, 3)))
+        if not args.skip_cpu:
+            rate, dt, cores, _ = cpu_oracle_rate(w, args.cpu_paths)
+            out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": f"{S} stations x {args.cpu_paths} paths of prism_ore_body, "
+                                             f"FP64 oracle, {dt:.1f} s wall"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 step / f64 accumulate", "data": "synthetic",
+                "config": {"workload": "prism_ore_body", "stations": S, "paths_per_station_per_step": Bp,
+                           "paths_per_station_total": total_paths, "step_m": 1.0, "h_m": 1.0,
+                           "l2": "flushed: 256 MiB memset before every step",
+                           "parallelism": "path-sharded replicas" if world > 1 else "1 GPU"},
+                "stations_per_s_at_1e-3": stations_per_s, "paths_per_s": paths_per_s,
+                "mean_path_steps_per_path": mean_steps_per_path,
+                "rel_se_u_median": float(np.median(se_u / np.abs(u))),
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "walk_ms_mean": statistics.mean(walk_ms),
+                "gpu_launches": 4 * args.steps, "status": st_code, "clocks": clocks}
+        line.update(out)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _max_op(world):
+    if world == 1:
+        return None
+    import torch.distributed as dist
+    return dist.ReduceOp.MAX
+
+
+def _sum_op(world):
+    if world == 1:
+        return None
+    import torch.distributed as dist
+    return dist.ReduceOp.SUM
+
+
+def fp64_comparison(M, w, dev):
+    """Stepping rate of the plain FP64 walk and of the mixed walk on the same
+    workload, free of exit-time tails: every path runs exactly `cap` RNG-steps
+    (max_steps), so all lanes stay busy for the whole launch."""
+    import torch
+    S = w.n_stations
+    out = {}
+    for name, prec, batch, cap in (("fp64", M.MCG_FP64, 4096, 256), ("mixed", M.MCG_MIXED, 8192, 16384)):
+        from paper_1709_07469_gb300.device import DeviceSolve
+        ds = DeviceSolve(w, batch=batch, precision=prec)
+        ds.opts.max_steps = cap
+        ds.reset()
+        ds.walk(10**5)
+        torch.cuda.synchronize(dev)
+        ds.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ds.walk(2 * 10**5)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        steps = float(ds.pp_steps[: S * batch].sum().item())
+        out[name] = {"path_steps_per_s": steps / (ms / 1e3), "paths": S * batch, "rng_steps_cap": cap}
+    out["mixed_over_fp64"] = out["mixed"]["path_steps_per_s"] / out["fp64"]["path_steps_per_s"]
+    out["how"] = "each path capped at a fixed RNG-step count so no lane idles (stepping rate, no exit tail)"
+    return out
+
+
+def e2e_solve(M, w, Bp, steps):
+    """The public one-call API with HOST stations and HOST results: each step
+    is mcgrav_solve over the step's batch (workspace allocation, host->device
+    copy of the stations, walk, reduction, device->host copy of the results)."""
+    import torch
+    prob = M.problem(w)
+    opts = M.options(w, precision=M.MCG_MIXED, batch_paths=Bp)
+    M.mcgrav_solve(prob, w.stations, Bp, w.dt, w.seed, opts)
+    torch.cuda.synchronize()
+    total_steps, t = 0.0, 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = M.mcgrav_solve(prob, w.stations, Bp, w.dt, w.seed, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        total_steps += float(r.path_steps.sum())
+    S = w.n_stations
+    return {"value": total_steps / t, "unit": UNIT, "h2d_bytes_per_step": S * 3 * 8,
+            "d2h_bytes_per_step": S * 6 * 8 + 4, "steps": steps,
+            "api": "mcgrav_solve (blocking, host buffers, one stream: exit-time tail not overlapped)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.capped_only:
+        import torch
+        from paper_1709_07469_gb300 import build as B
+        from paper_1709_07469_gb300 import mcgrav as M
+        from paper_1709_07469_gb300 import workloads as W
+        B.build()
+        M.load()
+        print(json.dumps(fp64_comparison(M, W.prism_ore_body(), torch.device("cuda", 0))), flush=True)
+        return 0
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

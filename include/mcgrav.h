@@ -179,15 +179,22 @@ MCG_API int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, c
  *   pp_d[i]     = (u(+h) - u(-h)) / (2h), or NaN without crn_gz (double)
  *   pp_steps[i] = Euler-Maruyama steps summed over the copies (int64)
  *   stations_dev: DEVICE, S x 3.   pp_*: DEVICE, length S*N.
+ *   work_dev    : DEVICE scratch of mcg_walk_work_bytes(S, N, precision)
+ *                 bytes (the mixed walk stores each copy's exit record
+ *                 there and a second kernel evaluates the exits); may be
+ *                 NULL when that size is 0.  Caller-owned, 256-byte aligned.
  *   status_dev  : DEVICE int32, OR-ed with (1 << status) for every path that
- *                 hit the step cap or produced a non-finite value; the
- *                 caller zeroes it.
+ *                 hit the step cap, started outside Omega or produced a
+ *                 non-finite value; the caller zeroes it.
  *   counter_dev : DEVICE uint64 work counter, zeroed by this call.
  * Allocates nothing. */
 MCG_API int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
              const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
-             const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps,
+             const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps, void* work_dev,
              int32_t* status_dev, unsigned long long* counter_dev);
+
+/* Bytes of scratch mcg_walk needs for S stations x N paths (0 for MCG_FP64). */
+MCG_API size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision);
 
 /* mcg_reduce: folds one batch of per-path values (S x N, as written by
  * mcg_walk) into the running station states (Eq. 7 and the sample

@@ -3,6 +3,7 @@
 // reduce batch by batch and copies the station results back.
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 
@@ -207,13 +208,21 @@ size_t mcg_workspace_bytes(int64_t S, int64_t batch)
     if (S <= 0 || batch <= 0) return 0;
     const size_t s = (size_t)S, n = (size_t)S * (size_t)batch;
     return align256(s * 3 * sizeof(double)) + align256(s * sizeof(mcg_station_state)) + 256 /* status+counter */ +
-           align256(s * 6 * sizeof(double)) + 2 * align256(n * sizeof(double)) + align256(n * sizeof(int64_t));
+           align256(s * 6 * sizeof(double)) + 2 * align256(n * sizeof(double)) + align256(n * sizeof(int64_t)) +
+           mcg_walk_work_bytes(S, batch, MCG_MIXED);
+}
+
+size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision)
+{
+    if (S <= 0 || N <= 0 || precision != MCG_MIXED) return 0;
+    const size_t n = (size_t)S * (size_t)N;
+    return align256(n * 3 * 8 * sizeof(float)) + align256(n * 3 * sizeof(double));
 }
 
 int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
              const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
-             const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps, int32_t* status_dev,
-             unsigned long long* counter_dev)
+             const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps, void* work_dev,
+             int32_t* status_dev, unsigned long long* counter_dev)
 {
     WalkParams P;
     int rc = make_params(domain, density, boundary, dt, seed, opts, P);
@@ -234,6 +243,13 @@ int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_bou
     P.pp_steps = pp_steps;
     P.status = status_dev;
     P.counter = counter_dev;
+    if (opts->precision == MCG_MIXED) {
+        if (!work_dev) return set_error(MCG_ERR_ARG, "the mixed walk needs work_dev (mcg_walk_work_bytes)");
+        if ((uintptr_t)work_dev % 256 != 0) return set_error(MCG_ERR_ARG, "work_dev must be 256-byte aligned");
+        const size_t n = (size_t)S * (size_t)N;
+        P.frec = (float*)work_dev;
+        P.drec = (double*)((char*)work_dev + align256(n * 3 * 8 * sizeof(float)));
+    }
     cudaStream_t st = (cudaStream_t)opts->stream;
     cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
@@ -282,8 +298,8 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
 
     int64_t batch = opts.batch_paths;
     if (batch <= 0) {
-        // per-path buffers of at most ~4 GiB per launch
-        const int64_t cap = (int64_t)((4ull << 30) / (24ull * (unsigned long long)S));
+        // per-path buffers and exit records of at most ~4 GiB per launch
+        const int64_t cap = (int64_t)((4ull << 30) / (152ull * (unsigned long long)S));
         batch = paths < cap ? paths : (cap > 0 ? cap : 1);
     }
     if (batch > paths) batch = paths;
@@ -311,6 +327,8 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     double* d_d = (double*)q;
     q += align256(n_ * sizeof(double));
     int64_t* d_steps = (int64_t*)q;
+    q += align256(n_ * sizeof(int64_t));
+    void* d_work = (void*)q;
 
     double* h_res = new double[6 * s_];
     int32_t h_status = 0;
@@ -324,8 +342,8 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
         }
         for (int64_t p0 = 0; p0 < paths && rc == MCG_OK; p0 += batch) {
             const int64_t nb = (paths - p0) < batch ? (paths - p0) : batch;
-            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &opts, d_u, d_d, d_steps, d_status,
-                          d_counter);
+            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &opts, d_u, d_d, d_steps, d_work,
+                          d_status, d_counter);
             if (rc == MCG_OK) rc = mcg_reduce(d_u, d_d, d_steps, S, nb, d_state, st);
         }
         if (rc) break;

@@ -48,6 +48,8 @@ struct WalkParams {
     int64_t* pp_steps;
     int32_t* status;
     unsigned long long* counter;
+    float* frec;                   // mixed walk: exit records (8 floats per copy per item)
+    double* drec;                  // mixed walk: flushed sums per copy per item
     volatile int32_t* cancel;
 };
 

@@ -26,6 +26,10 @@ namespace mcg {
 
 namespace {
 
+#ifndef MCG_MIXED_MINB
+#define MCG_MIXED_MINB 1
+#endif
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kNaN = __builtin_nan("");
 
@@ -62,6 +66,7 @@ __device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsi
         P.pp_u[item] = kNaN;
         P.pp_d[item] = kNaN;
         P.pp_steps[item] = 0;
+        if (P.drec) P.drec[item] = kNaN;  // the exit kernel then writes NaN too
         atomicOr(P.status, 1 << MCG_ERR_ARG);
     }
     return ok;
@@ -116,13 +121,15 @@ __device__ __noinline__ double exit_fp64(const WalkParams& P, const double* X, c
     return __dadd_rn(boundary_value(P, face, xs), -__dmul_rn(P.two_pi_G, I));
 }
 
-// Mixed walk: X, Y relative to the box centre in single precision; `acc`
-// is the flushed + partial sum S = rho_0 / 2 + sum_{n=1}^{N-1} rho_n, so the
-// trapezoid integral over the inside steps is dt (S - rho_{N-1} / 2).
-__device__ __noinline__ double exit_mixed(const WalkParams& P, float x0, float x1, float x2, float y0, float y1,
-                                          float y2, double acc, float rp)
+// Mixed walk exit (run by exit_mixed_kernel, one thread per path, so the
+// double-precision work is convergent): X, Y relative to the box centre in
+// single precision as the walk computed them; the flushed + partial sums give
+// S = rho_0 / 2 + sum_{n=1}^{N-1} rho_n, so the trapezoid integral over the
+// inside steps is dt (S - rho_{N-1} / 2).
+__device__ __forceinline__ double exit_mixed(const WalkParams& P, const float* Xf, const float* Yf, double flushed,
+                                             float partial, float rp)
 {
-    const float Xf[3] = {x0, x1, x2}, Yf[3] = {y0, y1, y2};
+    const double acc = flushed + (double)partial;
     double X[3], dW[3], xs[3];
     for (int k = 0; k < 3; ++k) {
         X[k] = (double)Xf[k];
@@ -132,7 +139,7 @@ __device__ __noinline__ double exit_mixed(const WalkParams& P, float x0, float x
     int face = -1;
     if (P.clip) {
         int kstar = -1;
-        double tmin = __longlong_as_double(0x7ff0000000000000LL), bstar = 0.0;
+        double tmin = __longlong_as_double(0x7ff0000000000000LL);
         for (int k = 0; k < 3; ++k) {
             if (!(fabsf(Yf[k]) >= P.half_f[k])) continue;  // the test that ended the walk
             const double b = (Yf[k] > 0.f ? P.hi[k] : P.lo[k]) - P.cen[k];
@@ -140,7 +147,6 @@ __device__ __noinline__ double exit_mixed(const WalkParams& P, float x0, float x
             if (t < tmin) {
                 tmin = t;
                 kstar = k;
-                bstar = b;
             }
         }
         if (kstar < 0) return kNaN;
@@ -149,7 +155,6 @@ __device__ __noinline__ double exit_mixed(const WalkParams& P, float x0, float x
         const bool upper = Yf[kstar] > 0.f;
         xs[kstar] = upper ? P.hi[kstar] : P.lo[kstar];
         face = 2 * kstar + (upper ? 1 : 0);
-        (void)bstar;
     } else {
         for (int k = 0; k < 3; ++k) xs[k] = P.cen[k] + (double)Yf[k];
     }
@@ -157,6 +162,26 @@ __device__ __noinline__ double exit_mixed(const WalkParams& P, float x0, float x
     const double rpd = (double)rp;
     const double I = P.dt * (acc - 0.5 * rpd) + 0.5 * theta * P.dt * (rpd + r);
     return boundary_value(P, face, xs) - P.two_pi_G * I;
+}
+
+// Exit records of the mixed walk (structure of arrays, item-major):
+//   frec[(8 c + f) * total + item], f = 0..2 X, 3..5 Y, 6 partial sum, 7 rho(X)
+//   drec[c * total + item]          flushed double sum (NaN: no result)
+__device__ __forceinline__ void put_exit(const WalkParams& P, int c, unsigned long long item, float x0, float x1,
+                                         float x2, float y0, float y1, float y2, float partial, float rp,
+                                         double flushed)
+{
+    float* f = P.frec + (size_t)8 * c * P.total + item;
+    const size_t T = P.total;
+    f[0] = x0;
+    f[T] = x1;
+    f[2 * T] = x2;
+    f[3 * T] = y0;
+    f[4 * T] = y1;
+    f[5 * T] = y2;
+    f[6 * T] = partial;
+    f[7 * T] = rp;
+    P.drec[(size_t)c * T + item] = flushed;
 }
 
 __device__ __forceinline__ void write_path(const WalkParams& P, unsigned long long item, double u0, double up,
@@ -254,10 +279,13 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision walk.
+// Mixed-precision walk: single-precision stepping, no double-precision work
+// except the flush of the partial sums, which all lanes of a warp do in the
+// same iteration (a warp-uniform branch).  A copy that leaves Omega writes an
+// exit record; exit_mixed_kernel turns the records into per-path values.
 // ---------------------------------------------------------------------------
 template <int RHO, bool CRN>
-__global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
+__global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
 {
     bool busy = false, exhausted = false;
     unsigned long long item = 0ull;
@@ -266,7 +294,6 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
     float S0 = 0.f, S1 = 0.f, S2 = 0.f;   // single-precision partial sums
     double D0 = 0.0, D1 = 0.0, D2 = 0.0;  // flushed sums
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // rho at the previous point
-    double u0 = kNaN, u1 = kNaN, u2 = kNaN;
     unsigned alive = 0u;
     int64_t steps = 0;
     const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2];
@@ -274,7 +301,8 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
     unsigned iter = 0u;
 
     for (;;) {
-        if ((++iter & 255u) == 0u && cancelled(P)) {
+        ++iter;
+        if ((iter & 255u) == 0u && cancelled(P)) {
             if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
             busy = false;
             exhausted = true;
@@ -295,13 +323,21 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
                 S2 = 0.5f * r2;
                 D1 = D2 = 0.0;
             }
-            u0 = u1 = u2 = kNaN;
             alive = CRN ? 7u : 1u;
             blk = 0u;
             steps = 0;
             busy = true;
         }
         if (!__any_sync(kFull, busy)) break;
+        if ((iter & 15u) == 0u) {  // warp-uniform flush, at most 64 steps per partial sum
+            D0 += (double)S0;
+            S0 = 0.f;
+            if (CRN) {
+                D1 += (double)S1;
+                D2 += (double)S2;
+                S1 = S2 = 0.f;
+            }
+        }
         if (!busy) continue;
 
         float z[12];
@@ -316,7 +352,7 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
                     r0 = rho_f32<RHO>(P, nx, ny, nz);
                     S0 += r0;
                 } else {
-                    u0 = exit_mixed(P, wx, wy, wz, nx, ny, nz, D0 + (double)S0, r0);
+                    put_exit(P, 0, item, wx, wy, wz, nx, ny, nz, S0, r0, D0);
                     alive &= ~1u;
                     steps += nstep;
                 }
@@ -328,7 +364,7 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
                         r1 = rho_f32<RHO>(P, nx, ny, zc);
                         S1 += r1;
                     } else {
-                        u1 = exit_mixed(P, wx, wy, wz + hf, nx, ny, zc, D1 + (double)S1, r1);
+                        put_exit(P, 1, item, wx, wy, wz + hf, nx, ny, zc, S1, r1, D1);
                         alive &= ~2u;
                         steps += nstep;
                     }
@@ -339,7 +375,7 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
                         r2 = rho_f32<RHO>(P, nx, ny, zc);
                         S2 += r2;
                     } else {
-                        u2 = exit_mixed(P, wx, wy, wz - hf, nx, ny, zc, D2 + (double)S2, r2);
+                        put_exit(P, 2, item, wx, wy, wz - hf, nx, ny, zc, S2, r2, D2);
                         alive &= ~4u;
                         steps += nstep;
                     }
@@ -351,24 +387,40 @@ __global__ void __launch_bounds__(128) walk_mixed_kernel(const WalkParams P)
             if (!alive) break;
         }
         ++blk;
-        if ((blk & 15u) == 0u) {  // flush every 64 steps
-            D0 += (double)S0;
-            S0 = 0.f;
-            if (CRN) {
-                D1 += (double)S1;
-                D2 += (double)S2;
-                S1 = S2 = 0.f;
-            }
-        }
         if (!alive) {
-            write_path(P, item, u0, u1, u2, steps);
+            P.pp_steps[item] = steps;
             busy = false;
         } else if (4 * (int64_t)blk >= P.max_steps) {
             atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
+            P.drec[item] = kNaN;  // copy 0 record marks "no result"
+            P.pp_steps[item] = steps + (int64_t)__popc(alive) * 4 * (int64_t)blk;
+            busy = false;
+        }
+    }
+}
+
+// Per-path values from the exit records (convergent double precision).
+__global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
+{
+    for (unsigned long long item = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; item < P.total;
+         item += (unsigned long long)gridDim.x * blockDim.x) {
+        double u[3] = {kNaN, kNaN, kNaN};
+        const int nc = P.crn ? 3 : 1;
+        const bool valid = !isnan(P.drec[item]);
+        if (valid) {
+            for (int c = 0; c < nc; ++c) {
+                const float* f = P.frec + (size_t)8 * c * P.total + item;
+                const size_t T = P.total;
+                const float X[3] = {f[0], f[T], f[2 * T]}, Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
+                u[c] = exit_mixed(P, X, Y, P.drec[(size_t)c * T + item], f[6 * T], f[7 * T]);
+            }
+            const double d = P.crn ? (u[1] - u[2]) / (2.0 * P.h) : kNaN;
+            P.pp_u[item] = u[0];
+            P.pp_d[item] = d;
+            if (!isfinite(u[0]) || (P.crn && !isfinite(d))) atomicOr(P.status, 1 << MCG_ERR_NONFINITE);
+        } else {
             P.pp_u[item] = kNaN;
             P.pp_d[item] = kNaN;
-            P.pp_steps[item] = steps;
-            busy = false;
         }
     }
 }
@@ -377,6 +429,14 @@ template <int RHO, bool CRN>
 cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t st)
 {
     walk_mixed_kernel<RHO, CRN><<<grid, block, 0, st>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned long long need = (P.total + 127ull) / 128ull;
+    const unsigned long long cap = (unsigned long long)sms * 16ull;
+    exit_mixed_kernel<<<(unsigned)(need < cap ? need : cap), 128, 0, st>>>(P);
     return cudaGetLastError();
 }
 

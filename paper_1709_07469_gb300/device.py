@@ -34,6 +34,9 @@ class DeviceSolve:
         self.status = torch.zeros(2, dtype=torch.int32, device=self.dev)
         self.counter = torch.zeros(1, dtype=torch.int64, device=self.dev)
         self.res = torch.empty((6, self.S), dtype=torch.float64, device=self.dev)
+        wb = M.mcg_walk_work_bytes(self.S, self.batch, precision)
+        # torch allocations are 512-byte aligned, as mcg_walk requires
+        self.work = torch.empty(max(wb, 1), dtype=torch.uint8, device=self.dev) if wb else None
 
     def reset(self):
         self.states.zero_()
@@ -43,7 +46,7 @@ class DeviceSolve:
         """Launch the walk for paths p0 .. p0+N-1 of every station."""
         N = self.batch if N is None else N
         M.mcg_walk(self.prob, self.stations, self.S, p0, N, self.w.dt, self.w.seed, self.opts,
-                   self.pp_u, self.pp_d, self.pp_steps, self.status, self.counter)
+                   self.pp_u, self.pp_d, self.pp_steps, self.work, self.status, self.counter)
         return N
 
     def reduce(self, N: int | None = None):

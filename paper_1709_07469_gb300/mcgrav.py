@@ -93,8 +93,10 @@ def load(path: str | None = None):
                                  P(mcg_options), P(mcg_result)]
     lib.mcgrav_solve.restype = C.c_int
     lib.mcg_walk.argtypes = [P(mcg_domain), P(mcg_density), P(mcg_boundary), vp, i64, i64, i64, d, u64,
-                             P(mcg_options), vp, vp, vp, vp, vp]
+                             P(mcg_options), vp, vp, vp, vp, vp, vp]
     lib.mcg_walk.restype = C.c_int
+    lib.mcg_walk_work_bytes.argtypes = [i64, i64, i32]
+    lib.mcg_walk_work_bytes.restype = C.c_size_t
     lib.mcg_reduce.argtypes = [vp, vp, vp, i64, i64, vp, vp]
     lib.mcg_reduce.restype = C.c_int
     lib.mcg_finalize.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
@@ -222,12 +224,16 @@ def mcgrav_solve(prob: Problem, stations: np.ndarray, paths: int, dt: float, see
 
 
 def mcg_walk(prob: Problem, stations_dev, S: int, p0: int, N: int, dt: float, seed: int, opts: mcg_options,
-             pp_u, pp_d, pp_steps, status_dev, counter_dev) -> int:
+             pp_u, pp_d, pp_steps, work_dev, status_dev, counter_dev) -> int:
     """Asynchronous walk launch on device buffers (torch tensors)."""
     rc = load().mcg_walk(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary), _ptr(stations_dev),
                          S, p0, N, dt, seed & 0xFFFFFFFFFFFFFFFF, C.byref(opts), _ptr(pp_u), _ptr(pp_d),
-                         _ptr(pp_steps), _ptr(status_dev), _ptr(counter_dev))
+                         _ptr(pp_steps), _ptr(work_dev), _ptr(status_dev), _ptr(counter_dev))
     return _check(rc)
+
+
+def mcg_walk_work_bytes(S: int, N: int, precision: int) -> int:
+    return int(load().mcg_walk_work_bytes(S, N, precision))
 
 
 def mcg_reduce(pp_u, pp_d, pp_steps, S: int, N: int, states_dev, stream=None) -> int:

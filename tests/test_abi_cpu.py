@@ -66,7 +66,10 @@ def test_defaults_and_workspace(lib):
     assert o.max_steps == 1 << 31
     assert M.mcg_workspace_bytes(0, 10) == 0
     b = M.mcg_workspace_bytes(30, 1000)
-    assert b >= 30 * 1000 * 24 and b < 30 * 1000 * 24 + 64 * 1024
+    # per path: u, d, steps (24 B) + the mixed walk's exit records (3 x 40 B)
+    assert b >= 30 * 1000 * 144 and b < 30 * 1000 * 144 + 64 * 1024
+    assert M.mcg_walk_work_bytes(30, 1000, M.MCG_FP64) == 0
+    assert M.mcg_walk_work_bytes(30, 1000, M.MCG_MIXED) >= 30 * 1000 * 120
     assert "sm_103a" in M.version()
 
 
