@@ -22,9 +22,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
-        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        // one 32x32->64 multiply gives both halves of each product
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += kPhiloxW0;
         k1 += kPhiloxW1;
     }
@@ -91,20 +92,25 @@ __device__ __forceinline__ float cos_approx(float x)
     return y;
 }
 
-__device__ __forceinline__ float u01_f32(uint32_t w)
+// 1 + (w >> 9) 2^-23 in [1, 2): exponent bits 0x7F funnel-shifted in above
+// the top 23 bits of w.
+__device__ __forceinline__ float one_plus_mantissa(uint32_t w)
 {
-    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994f;
+    return __uint_as_float(__funnelshift_r(w, 0x7Fu, 9));
 }
+__device__ __forceinline__ float u01_f32(uint32_t w) { return one_plus_mantissa(w) - 0.99999994f; }
 // u - 1/2, exact: (1 + m 2^-23) - 1.5 is exact, + 2^-24 lands on the grid.
-__device__ __forceinline__ float u01m_f32(uint32_t w)
-{
-    return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.5f) + 0x1p-24f;
-}
+__device__ __forceinline__ float u01m_f32(uint32_t w) { return (one_plus_mantissa(w) - 1.5f) + 0x1p-24f; }
+
+// The angle 2 pi (u2 - 1/2) = 2 pi v - 2 pi (1.5 - 2^-24), v = 1 + m 2^-23,
+// as one fused multiply-add (within one rounding of the exact angle).
+constexpr float kTwoPi = 6.28318530717958648f;
+constexpr float kAngleOffset = (float)(-6.283185307179586476925 * (1.5 - 0x1p-24));
 
 __device__ __forceinline__ void box_muller_f32(uint32_t w1, uint32_t w2, float lnscale, float& z0, float& z1)
 {
     const float nr = -sqrt_approx(lnscale * lg2_approx(u01_f32(w1)));  // -sd sqrt(-2 ln u1)
-    const float a = 6.28318530717958648f * u01m_f32(w2);
+    const float a = fmaf(one_plus_mantissa(w2), kTwoPi, kAngleOffset);
     z0 = nr * cos_approx(a);
     z1 = nr * sin_approx(a);
 }
@@ -144,6 +150,42 @@ __device__ __forceinline__ float rho_f32(const WalkParams& P, float x, float y, 
         return __ldg(P.grid + idx);
     } else {
         return 0.0f;
+    }
+}
+
+// Density at the three common-random-number copies (x, y, z), (x, y, z+h),
+// (x, y, z-h): the x / y part is computed once.
+template <int RHO>
+__device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, float z, float h, float& ra,
+                                         float& rb, float& rc)
+{
+    if constexpr (RHO == MCG_RHO_SPHERE) {
+        const float dx = x - P.sc_f[0], dy = y - P.sc_f[1], dz = z - P.sc_f[2];
+        const float q = dx * dx + dy * dy;
+        const float za = dz, zb = dz + h, zc = dz - h;
+        ra = (q + za * za < P.srad2_f) ? P.rho0_f : 0.0f;
+        rb = (q + zb * zb < P.srad2_f) ? P.rho0_f : 0.0f;
+        rc = (q + zc * zc < P.srad2_f) ? P.rho0_f : 0.0f;
+    } else if constexpr (RHO == MCG_RHO_PRISM) {
+        const bool inxy = x >= P.plo_f[0] && x < P.phi_f[0] && y >= P.plo_f[1] && y < P.phi_f[1];
+        const float zb = z + h, zc = z - h;
+        ra = (inxy && z >= P.plo_f[2] && z < P.phi_f[2]) ? P.rho0_f : 0.0f;
+        rb = (inxy && zb >= P.plo_f[2] && zb < P.phi_f[2]) ? P.rho0_f : 0.0f;
+        rc = (inxy && zc >= P.plo_f[2] && zc < P.phi_f[2]) ? P.rho0_f : 0.0f;
+    } else if constexpr (RHO == MCG_RHO_VOXEL) {
+        const float tx = floorf((x - P.org_f[0]) * P.inv_sp_f[0]);
+        const float ty = floorf((y - P.org_f[1]) * P.inv_sp_f[1]);
+        const bool inxy = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny;
+        const int base = (int)tx + P.nx * (int)ty;
+        const float za = floorf((z - P.org_f[2]) * P.inv_sp_f[2]);
+        const float zb = floorf((z + h - P.org_f[2]) * P.inv_sp_f[2]);
+        const float zc = floorf((z - h - P.org_f[2]) * P.inv_sp_f[2]);
+        const int plane = P.nx * P.ny;
+        ra = (inxy && za >= 0.f && za < (float)P.nz) ? __ldg(P.grid + base + plane * (int)za) : 0.0f;
+        rb = (inxy && zb >= 0.f && zb < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zb) : 0.0f;
+        rc = (inxy && zc >= 0.f && zc < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zc) : 0.0f;
+    } else {
+        ra = rb = rc = 0.0f;
     }
 }
 

@@ -27,7 +27,7 @@ namespace mcg {
 namespace {
 
 #ifndef MCG_MIXED_MINB
-#define MCG_MIXED_MINB 1
+#define MCG_MIXED_MINB 4
 #endif
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -279,10 +279,14 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision walk: single-precision stepping, no double-precision work
-// except the flush of the partial sums, which all lanes of a warp do in the
-// same iteration (a warp-uniform branch).  A copy that leaves Omega writes an
-// exit record; exit_mixed_kernel turns the records into per-path values.
+// Mixed-precision walk: single-precision stepping and no double-precision
+// arithmetic in the step loop.  The three common-random-number copies are
+// updated branch-free; exits (rare) take a side branch that writes an exit
+// record, which exit_mixed_kernel turns into per-path values.  A warp runs up
+// to 16 blocks (64 steps) between refills; after them it flushes the
+// single-precision partial sums into the double sums (a real, warp-uniform
+// branch, so the slow double-precision unit sees one instruction per copy per
+// 64 steps).
 // ---------------------------------------------------------------------------
 template <int RHO, bool CRN>
 __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
@@ -297,12 +301,11 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
     unsigned alive = 0u;
     int64_t steps = 0;
     const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2];
-    const float hf = P.h_f;
-    unsigned iter = 0u;
+    const float hf = CRN ? P.h_f : 0.0f;
+    unsigned round = 0u;
 
     for (;;) {
-        ++iter;
-        if ((iter & 255u) == 0u && cancelled(P)) {
+        if ((++round & 15u) == 0u && cancelled(P)) {
             if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
             busy = false;
             exhausted = true;
@@ -313,88 +316,76 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             wx = (float)(P.stations[3 * s + 0] - P.cen[0]);
             wy = (float)(P.stations[3 * s + 1] - P.cen[1]);
             wz = (float)(P.stations[3 * s + 2] - P.cen[2]);
-            r0 = rho_f32<RHO>(P, wx, wy, wz);
+            rho3_f32<RHO>(P, wx, wy, wz, hf, r0, r1, r2);
             S0 = 0.5f * r0;
-            D0 = 0.0;
-            if (CRN) {
-                r1 = rho_f32<RHO>(P, wx, wy, wz + hf);
-                r2 = rho_f32<RHO>(P, wx, wy, wz - hf);
-                S1 = 0.5f * r1;
-                S2 = 0.5f * r2;
-                D1 = D2 = 0.0;
-            }
+            S1 = 0.5f * r1;
+            S2 = 0.5f * r2;
+            D0 = D1 = D2 = 0.0;
             alive = CRN ? 7u : 1u;
             blk = 0u;
             steps = 0;
             busy = true;
         }
         if (!__any_sync(kFull, busy)) break;
-        if ((iter & 15u) == 0u) {  // warp-uniform flush, at most 64 steps per partial sum
-            D0 += (double)S0;
-            S0 = 0.f;
-            if (CRN) {
-                D1 += (double)S1;
-                D2 += (double)S2;
-                S1 = S2 = 0.f;
-            }
-        }
-        if (!busy) continue;
 
-        float z[12];
-        normals12_f32(s, p, blk, P.key0, P.key1, P.lnscale_f, z);
+#pragma unroll 1
+        for (int k = 0; k < 16; ++k) {
+            if (busy) {
+                float z[12];
+                normals12_f32(s, p, blk, P.key0, P.key1, P.lnscale_f, z);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float nx = wx + z[3 * m], ny = wy + z[3 * m + 1], nz = wz + z[3 * m + 2];
-            const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
-            const int64_t nstep = 4 * (int64_t)blk + m + 1;
-            if (alive & 1u) {
-                if (inxy && fabsf(nz) < hz) {
-                    r0 = rho_f32<RHO>(P, nx, ny, nz);
-                    S0 += r0;
-                } else {
-                    put_exit(P, 0, item, wx, wy, wz, nx, ny, nz, S0, r0, D0);
-                    alive &= ~1u;
-                    steps += nstep;
+                for (int m = 0; m < 4; ++m) {
+                    const float nx = wx + z[3 * m], ny = wy + z[3 * m + 1], nz = wz + z[3 * m + 2];
+                    const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
+                    unsigned ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
+                    if (CRN) {
+                        ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
+                        ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
+                    }
+                    const unsigned out = alive & ~ins;
+                    if (out) {  // rare: some copy left Omega on this step
+                        const int64_t nstep = 4 * (int64_t)blk + m + 1;
+                        if (out & 1u) put_exit(P, 0, item, wx, wy, wz, nx, ny, nz, S0, r0, D0);
+                        if (CRN && (out & 2u)) put_exit(P, 1, item, wx, wy, wz + hf, nx, ny, nz + hf, S1, r1, D1);
+                        if (CRN && (out & 4u)) put_exit(P, 2, item, wx, wy, wz - hf, nx, ny, nz - hf, S2, r2, D2);
+                        steps += nstep * (int64_t)__popc(out);
+                        alive &= ins;
+                    }
+                    float ra, rb, rc;
+                    rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
+                    S0 += ra;
+                    r0 = ra;
+                    if (CRN) {
+                        S1 += rb;
+                        S2 += rc;
+                        r1 = rb;
+                        r2 = rc;
+                    }
+                    wx = nx;
+                    wy = ny;
+                    wz = nz;
+                    if (!alive) break;
+                }
+                ++blk;
+                if (!alive) {
+                    P.pp_steps[item] = steps;
+                    busy = false;
+                } else if (4 * (int64_t)blk >= P.max_steps) {
+                    atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
+                    P.drec[item] = kNaN;  // copy 0 record marks "no result"
+                    P.pp_steps[item] = steps + (int64_t)__popc(alive) * 4 * (int64_t)blk;
+                    busy = false;
                 }
             }
-            if (CRN) {
-                if (alive & 2u) {
-                    const float zc = nz + hf;
-                    if (inxy && fabsf(zc) < hz) {
-                        r1 = rho_f32<RHO>(P, nx, ny, zc);
-                        S1 += r1;
-                    } else {
-                        put_exit(P, 1, item, wx, wy, wz + hf, nx, ny, zc, S1, r1, D1);
-                        alive &= ~2u;
-                        steps += nstep;
-                    }
-                }
-                if (alive & 4u) {
-                    const float zc = nz - hf;
-                    if (inxy && fabsf(zc) < hz) {
-                        r2 = rho_f32<RHO>(P, nx, ny, zc);
-                        S2 += r2;
-                    } else {
-                        put_exit(P, 2, item, wx, wy, wz - hf, nx, ny, zc, S2, r2, D2);
-                        alive &= ~4u;
-                        steps += nstep;
-                    }
-                }
-            }
-            wx = nx;
-            wy = ny;
-            wz = nz;
-            if (!alive) break;
+            if (__any_sync(kFull, !busy && !exhausted)) break;  // a lane wants new work
         }
-        ++blk;
-        if (!alive) {
-            P.pp_steps[item] = steps;
-            busy = false;
-        } else if (4 * (int64_t)blk >= P.max_steps) {
-            atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
-            P.drec[item] = kNaN;  // copy 0 record marks "no result"
-            P.pp_steps[item] = steps + (int64_t)__popc(alive) * 4 * (int64_t)blk;
-            busy = false;
+        // warp-uniform flush of the partial sums (at most 16 blocks = 64 steps each)
+        D0 += (double)S0;
+        S0 = 0.f;
+        if (CRN) {
+            D1 += (double)S1;
+            D2 += (double)S2;
+            S1 = S2 = 0.f;
         }
     }
 }
