@@ -39,8 +39,12 @@ METRIC = "path-steps/s & stations/s at 1e-3 rel std err, mixed vs FP64 walk; p50
 UNIT = "path-steps/s"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# Ideal lane-instruction count per path-step of the mixed walk (model in the design doc).
-OPS_PER_PATH_STEP = 29.0
+# Ideal lane-instruction count of the mixed walk per RNG-step (one Gaussian
+# triple advancing the three common-random-number copies), model in the design doc:
+# Philox 30 + uniforms 6 + Box-Muller 12 + position 3 + exit test 7 +
+# density 13 + trapezoid 3 = 74; per path-step (3 copies) 74 / 3.
+OPS_PER_RNG_STEP = 74.0
+OPS_PER_PATH_STEP = OPS_PER_RNG_STEP / 3.0
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -282,15 +286,21 @@ def run_ours(args):
     out = {}
     if rank == 0:
         # roofline of the dominant kernel (the mixed walk): model lane-instructions
-        # per launch / average walk-kernel duration, against one warp-instruction
-        # per clock per scheduler at the maximum SM clock
+        # per launch / time per launch, against one warp-instruction per clock
+        # per scheduler at the maximum SM clock.  Launches overlap on two
+        # streams (one batch's exit tail runs beside the next batch), so the
+        # time per launch is the timed region / K; the event time of each
+        # launch (which includes the overlap) is reported beside it.
         per_launch_ops = OPS_PER_PATH_STEP * path_steps_local / args.steps
-        avg_walk_s = statistics.mean(walk_ms) / 1e3
-        achieved = per_launch_ops / avg_walk_s / 1e12
+        per_launch_s = (elapsed_ms / args.steps) / 1e3
+        achieved = per_launch_ops / per_launch_s / 1e12
         peak = SM_COUNT * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
                            "frac": achieved / peak, "traffic": None,
                            "kernel": "walk_mixed_kernel<PRISM,crn>",
+                           "ops_per_rng_step": OPS_PER_RNG_STEP,
+                           "launch_time": "timed region / K (two-stream pipeline)",
+                           "launch_event_ms_mean": statistics.mean(walk_ms),
                            "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (recipe unit counts)"}
         if not args.skip_fp64:
             out["fp64_walk"] = fp64_comparison(M, w, dev)
