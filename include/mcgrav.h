@@ -196,6 +196,34 @@ MCG_API int mcg_walk(const mcg_domain* domain, const mcg_density* density, const
 /* Bytes of scratch mcg_walk needs for S stations x N paths (0 for MCG_FP64). */
 MCG_API size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision);
 
+/* mcg_walk_static: mcg_walk for callers that cannot allocate device memory.
+ * No counterpart in the paper: this is a deployment variant of the walk.
+ * Some callers only hand over the buffers they were given and may not call
+ * cudaMalloc themselves: plug-in hosts that pass fixed input/output arrays,
+ * services whose memory manager owns the whole device budget, and code on a
+ * latency-critical path where an allocation would synchronise the device.
+ * This entry point takes the same inputs and writes the same outputs as
+ * mcg_walk (pp_u, pp_d, pp_steps, status_dev), but keeps its scratch -- the
+ * work counter and the mixed walk's exit records -- in one fixed device
+ * array inside the library (64 MiB, held by every GPU that loads the library
+ * until the process exits).  It allocates nothing.
+ *   - S * N may not exceed mcg_walk_static_max_items() (about 5.6e5 paths);
+ *     larger requests return MCG_ERR_ARG with a message saying so.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     the call zeroes the counter itself.  Calls that overlap on the GPU
+ *     (other streams, other threads) race on it: serialise them.
+ * Asynchronous on opts->stream like mcg_walk. */
+MCG_API int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+                            const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
+                            const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps,
+                            int32_t* status_dev);
+
+/* Largest S * N mcg_walk_static accepts. */
+MCG_API int64_t mcg_walk_static_max_items(void);
+
 /* mcg_reduce: folds one batch of per-path values (S x N, as written by
  * mcg_walk) into the running station states (Eq. 7 and the sample
  * variance): per station a fixed-order two-pass mean / sum of squares with

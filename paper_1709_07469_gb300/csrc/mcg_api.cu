@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -174,6 +175,54 @@ int status_from_bits(int bits)
     if (bits & (1 << MCG_ERR_NONFINITE)) return set_error(MCG_ERR_NONFINITE, "a per-path value was not finite");
     if (bits & (1 << MCG_ERR_CANCELLED)) return set_error(MCG_ERR_CANCELLED, "cancelled");
     return MCG_OK;
+}
+
+}  // namespace
+}  // namespace mcg
+
+// ---------------------------------------------------------------------------
+// Fixed scratch for mcg_walk_static: a file-scope device array that every GPU
+// loading this library holds until the process exits.  Layout: the walk's
+// work counter (first 256 bytes), then the mixed walk's exit records.
+// ---------------------------------------------------------------------------
+#define MCG_STATIC_SCRATCH_BYTES (64u << 20)
+static __device__ __align__(256) unsigned char mcg_static_scratch[MCG_STATIC_SCRATCH_BYTES];
+
+namespace mcg {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_base[kMaxDevices] = {};
+
+// Device address of mcg_static_scratch on `dev` (the current device).  The
+// host-side symbol is only a stand-in for the array, so the address is
+// looked up once per device with that device current.
+int static_scratch(int dev, unsigned char** base)
+{
+    if (dev < 0 || dev >= kMaxDevices) return set_error(MCG_ERR_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_base[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, mcg_static_scratch);
+        if (e != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            return set_error(MCG_ERR_CUDA, "cudaGetSymbolAddress(mcg_static_scratch) on device %d: %s", dev,
+                             cudaGetErrorString(e));
+        }
+        g_static_base[dev] = ptr;
+    }
+    *base = (unsigned char*)g_static_base[dev];
+    return MCG_OK;
+}
+
+// Largest S * N whose exit records fit behind the 256-byte counter slot.
+int64_t static_max_items()
+{
+    const size_t avail = (size_t)MCG_STATIC_SCRATCH_BYTES - 256;
+    int64_t n = (int64_t)((avail - 512) / (3 * 8 * sizeof(float) + 3 * sizeof(double)));
+    while (n > 0 && align256((size_t)n * 3 * 8 * sizeof(float)) + align256((size_t)n * 3 * sizeof(double)) > avail) --n;
+    return n;
 }
 
 }  // namespace
@@ -390,6 +439,54 @@ int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblo
     if (!out) return set_error(MCG_ERR_ARG, "null output");
     cudaError_t e = launch_normals(seed, s, p, b0, nblocks, precision, out, (cudaStream_t)stream);
     return e == cudaSuccess ? MCG_OK : cuda_fail(e, "normals kernel launch");
+}
+
+int64_t mcg_walk_static_max_items(void) { return static_max_items(); }
+
+int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+                    const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
+                    const mcg_options* opts, double* pp_u, double* pp_d, int64_t* pp_steps, int32_t* status_dev)
+{
+    WalkParams P;
+    int rc = make_params(domain, density, boundary, dt, seed, opts, P);
+    if (rc) return rc;
+    if (S < 0 || N < 0 || p0 < 0) return set_error(MCG_ERR_ARG, "S, N and p0 must be non-negative");
+    if (p0 + N > (int64_t)1 << 32) return set_error(MCG_ERR_ARG, "path indices must fit in 32 bits");
+    if (S > (int64_t)1 << 32) return set_error(MCG_ERR_ARG, "station indices must fit in 32 bits");
+    if (S == 0 || N == 0) return MCG_OK;
+    const int64_t max_items = static_max_items();
+    if (S > max_items / N)
+        return set_error(MCG_ERR_ARG, "mcg_walk_static: S * N = %lld exceeds the fixed scratch limit of %lld paths",
+                         (long long)S * (long long)N, (long long)max_items);
+    if (!stations_dev || !pp_u || !pp_d || !pp_steps || !status_dev)
+        return set_error(MCG_ERR_ARG, "null device buffer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    unsigned char* base = nullptr;
+    if ((rc = static_scratch(dev, &base))) return rc;
+    const size_t n = (size_t)S * (size_t)N;
+    P.stations = stations_dev;
+    P.S = S;
+    P.N = N;
+    P.p0 = p0;
+    P.total = (unsigned long long)n;
+    P.pp_u = pp_u;
+    P.pp_d = pp_d;
+    P.pp_steps = pp_steps;
+    P.status = status_dev;
+    P.counter = (unsigned long long*)base;
+    if (opts->precision == MCG_MIXED) {
+        P.frec = (float*)(base + 256);
+        P.drec = (double*)(base + 256 + align256(n * 3 * 8 * sizeof(float)));
+    }
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    // the counter must start at zero; the exit records are written before use
+    e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(static counter)");
+    e = launch_walk(P, opts->precision, opts->block ? opts->block : 128, st);
+    if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+    return MCG_OK;
 }
 
 }  // extern "C"

@@ -97,6 +97,11 @@ def load(path: str | None = None):
     lib.mcg_walk.restype = C.c_int
     lib.mcg_walk_work_bytes.argtypes = [i64, i64, i32]
     lib.mcg_walk_work_bytes.restype = C.c_size_t
+    lib.mcg_walk_static.argtypes = [P(mcg_domain), P(mcg_density), P(mcg_boundary), vp, i64, i64, i64, d, u64,
+                                    P(mcg_options), vp, vp, vp, vp]
+    lib.mcg_walk_static.restype = C.c_int
+    lib.mcg_walk_static_max_items.argtypes = []
+    lib.mcg_walk_static_max_items.restype = C.c_int64
     lib.mcg_reduce.argtypes = [vp, vp, vp, i64, i64, vp, vp]
     lib.mcg_reduce.restype = C.c_int
     lib.mcg_finalize.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
@@ -234,6 +239,19 @@ def mcg_walk(prob: Problem, stations_dev, S: int, p0: int, N: int, dt: float, se
 
 def mcg_walk_work_bytes(S: int, N: int, precision: int) -> int:
     return int(load().mcg_walk_work_bytes(S, N, precision))
+
+
+def mcg_walk_static(prob: Problem, stations_dev, S: int, p0: int, N: int, dt: float, seed: int, opts: mcg_options,
+                    pp_u, pp_d, pp_steps, status_dev, allow=()) -> int:
+    """The walk with the library's fixed scratch (no device allocation)."""
+    rc = load().mcg_walk_static(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary),
+                                _ptr(stations_dev), S, p0, N, dt, seed & 0xFFFFFFFFFFFFFFFF, C.byref(opts),
+                                _ptr(pp_u), _ptr(pp_d), _ptr(pp_steps), _ptr(status_dev))
+    return _check(rc, allow)
+
+
+def mcg_walk_static_max_items() -> int:
+    return int(load().mcg_walk_static_max_items())
 
 
 def mcg_reduce(pp_u, pp_d, pp_steps, S: int, N: int, states_dev, stream=None) -> int:
