@@ -258,6 +258,40 @@ MCG_API int mcg_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint
 MCG_API int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblocks, int32_t precision,
                 void* out, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Heterogeneous model set-up (once per model, outside the walk).            */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device scratch mcg_grf_density needs for an nx x ny x nz grid. */
+MCG_API size_t mcg_grf_work_bytes(int64_t nx, int64_t ny, int64_t nz);
+
+/* mcg_grf_density: a Gaussian-random-field density model on an nx x ny x nz
+ * voxel grid (x fastest), the heterogeneous subsurface of the survey
+ * workloads (the paper's models are a single homogeneous cube, Sec. 3):
+ *   1. white noise N(0,1): voxels 4q..4q+3 take the two Box-Muller pairs of
+ *      Philox4x32-10 counter (q, 0, 0, 1) under key (lo32 seed, hi32 seed);
+ *   2. separable Gaussian smoothing of std sigma_vox voxels, taps |m| <=
+ *      ceil(3 sigma_vox) (at most 63), weights summing to 1, zero outside;
+ *   3. rescaled to zero mean and unit population standard deviation;
+ *   4. rho = amp (exp(Z) - 1), stored as float32.
+ * grid_out: DEVICE float32, nx*ny*nz.  work: DEVICE, mcg_grf_work_bytes.
+ * Asynchronous on `stream`.  Allocates nothing. */
+MCG_API int mcg_grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, double sigma_vox, double amp,
+                            float* grid_out, void* work, void* stream);
+
+/* mcg_boundary_tables: Dirichlet data for MCG_G_TABLE -- the potential
+ * Phi = -G sum_voxels rho_v [[[F]]]_v of the voxel model (prism summation,
+ * the closed form the paper compares against, Sec. 1 and Sec. 4.2) at the
+ * nu x nv nodes of each face of `domain` (layout as MCG_G_TABLE).  Voxels
+ * whose centre lies within `near_cells` cell diagonals of a node use the
+ * exact prism potential in double precision; farther voxels, which must be
+ * cubes or close to them, use their point-mass term rho_v V / r in single
+ * precision, whose relative error for a cube is O((d/r)^4).  Supports
+ * nx <= 128.  faces_out: DEVICE float32, 6 nv nu.  density->grid: DEVICE.
+ * Asynchronous on `stream`.  Allocates nothing. */
+MCG_API int mcg_boundary_tables(const mcg_domain* domain, const mcg_density* density, int32_t nu, int32_t nv,
+                                double near_cells, float* faces_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -441,6 +441,24 @@ int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblo
     return e == cudaSuccess ? MCG_OK : cuda_fail(e, "normals kernel launch");
 }
 
+size_t mcg_grf_work_bytes(int64_t nx, int64_t ny, int64_t nz)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
+    return (size_t)2 * (size_t)nx * (size_t)ny * (size_t)nz * sizeof(double) + 256;
+}
+
+int mcg_grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, double sigma_vox, double amp,
+                    float* grid_out, void* work, void* stream)
+{
+    return grf_density(seed, nx, ny, nz, sigma_vox, amp, grid_out, (double*)work, (cudaStream_t)stream);
+}
+
+int mcg_boundary_tables(const mcg_domain* domain, const mcg_density* density, int32_t nu, int32_t nv,
+                        double near_cells, float* faces_out, void* stream)
+{
+    return boundary_tables(domain, density, nu, nv, near_cells, faces_out, (cudaStream_t)stream);
+}
+
 int64_t mcg_walk_static_max_items(void) { return static_max_items(); }
 
 int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,

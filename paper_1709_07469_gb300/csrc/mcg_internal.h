@@ -68,6 +68,12 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 cudaError_t launch_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblocks, int precision,
                            void* out, cudaStream_t st);
 
+// Set-up launchers (mcg_setup.cu).
+int grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, double sigma_vox, double amp, float* grid_out,
+                double* work, cudaStream_t st);
+int boundary_tables(const mcg_domain* d, const mcg_density* rho, int32_t nu, int32_t nv, double near_cells,
+                    float* faces_out, cudaStream_t st);
+
 // Thread-local error message (mcg_api.cu).
 int set_error(int code, const char* fmt, ...);
 

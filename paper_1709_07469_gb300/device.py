@@ -83,3 +83,19 @@ class DeviceSolve:
         k = self.S * N
         return (self.pp_u[:k].cpu().numpy().reshape(self.S, N), self.pp_d[:k].cpu().numpy().reshape(self.S, N),
                 self.pp_steps[:k].cpu().numpy().reshape(self.S, N))
+
+
+def voxel_model(w, device: str = "cuda", stream=None, near_cells: float = 4.0):
+    """Device-resident heterogeneous model of a voxel workload: the GRF density
+    grid [nz, ny, nx] and the boundary tables [6, nv, nu] (float32), built by
+    mcg_grf_density and mcg_boundary_tables."""
+    nx, ny, nz = w.grid_shape
+    dev = torch.device(device)
+    grid = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    work = torch.empty(M.mcg_grf_work_bytes(nx, ny, nz), dtype=torch.uint8, device=dev)
+    M.mcg_grf_density(w.grid_seed, nx, ny, nz, w.grid_sigma_vox, w.grid_amp, grid, work, stream)
+    nu, nv = w.table_n
+    faces = torch.empty((6, nv, nu), dtype=torch.float32, device=dev)
+    prob = M.problem(w.with_(g_kind="zero"), grid=grid)
+    M.mcg_boundary_tables(prob, nu, nv, near_cells, faces, stream)
+    return grid, faces

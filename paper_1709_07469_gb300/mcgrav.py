@@ -102,6 +102,12 @@ def load(path: str | None = None):
     lib.mcg_walk_static.restype = C.c_int
     lib.mcg_walk_static_max_items.argtypes = []
     lib.mcg_walk_static_max_items.restype = C.c_int64
+    lib.mcg_grf_work_bytes.argtypes = [i64, i64, i64]
+    lib.mcg_grf_work_bytes.restype = C.c_size_t
+    lib.mcg_grf_density.argtypes = [u64, i64, i64, i64, d, d, vp, vp, vp]
+    lib.mcg_grf_density.restype = C.c_int
+    lib.mcg_boundary_tables.argtypes = [P(mcg_domain), P(mcg_density), i32, i32, d, vp, vp]
+    lib.mcg_boundary_tables.restype = C.c_int
     lib.mcg_reduce.argtypes = [vp, vp, vp, i64, i64, vp, vp]
     lib.mcg_reduce.restype = C.c_int
     lib.mcg_finalize.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
@@ -276,3 +282,18 @@ def mcg_philox(ctr_dev, key_dev, n: int, out_dev, stream=None) -> int:
 def mcg_normals(seed: int, s: int, p: int, b0: int, nblocks: int, precision: int, out_dev, stream=None) -> int:
     return _check(load().mcg_normals(seed & 0xFFFFFFFFFFFFFFFF, s, p, b0, nblocks, precision, _ptr(out_dev),
                                      _stream_handle(stream)))
+
+
+def mcg_grf_work_bytes(nx: int, ny: int, nz: int) -> int:
+    return int(load().mcg_grf_work_bytes(nx, ny, nz))
+
+
+def mcg_grf_density(seed: int, nx: int, ny: int, nz: int, sigma_vox: float, amp: float, grid_out, work,
+                    stream=None) -> int:
+    return _check(load().mcg_grf_density(seed & 0xFFFFFFFFFFFFFFFF, nx, ny, nz, sigma_vox, amp, _ptr(grid_out),
+                                         _ptr(work), _stream_handle(stream)))
+
+
+def mcg_boundary_tables(prob: Problem, nu: int, nv: int, near_cells: float, faces_out, stream=None) -> int:
+    return _check(load().mcg_boundary_tables(C.byref(prob.domain), C.byref(prob.density), nu, nv, near_cells,
+                                             _ptr(faces_out), _stream_handle(stream)))

@@ -1,0 +1,133 @@
+"""GPU set-up of the heterogeneous model against the oracle (through the C ABI).
+
+* GRF density: element by element against the oracle's double-precision
+  field; both sides take the same operations in the same order except the
+  order of the mean / variance sums and exp (a few ulp), so the float grids
+  agree to 2 ulp.
+* Boundary tables: sampled nodes of every face against the oracle's exact
+  direct prism sum over all voxels.  The GPU uses the exact prism within
+  `near_cells` cell diagonals and the point-mass term beyond; for cubic cells
+  the point-mass error is below (d/r)^4 / 10 per voxel at r >= 4 diagonals,
+  i.e. < 5e-6 relative of a node value; the tolerance adds float rounding.
+* Walk on the voxel model (grid from the oracle, smooth synthetic tables as
+  plain input): per-path FP64 parity and the mixed paired test.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_07469_gb300 import build as B
+from paper_1709_07469_gb300 import mcgrav as M
+from paper_1709_07469_gb300 import workloads as W
+from paper_1709_07469_gb300.device import DeviceSolve, voxel_model
+from tests.helpers import oracle_spec, smooth_tables
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    B.build()
+    M.load()
+
+
+def gpu_grf(seed, nx, ny, nz, sigma, amp=300.0):
+    grid = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+    work = torch.empty(M.mcg_grf_work_bytes(nx, ny, nz), dtype=torch.uint8, device="cuda")
+    M.mcg_grf_density(seed, nx, ny, nz, sigma, amp, grid, work)
+    torch.cuda.synchronize()
+    return grid.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,sigma", [((128, 128, 64), 5.0), ((37, 29, 11), 1.7)])
+def test_grf_matches_oracle(shape, sigma):
+    nx, ny, nz = shape
+    got = gpu_grf(5, nx, ny, nz, sigma)
+    want = oracle.grf_density(5, nx, ny, nz, sigma_vox=sigma, amp=300.0)
+    ulp = np.spacing(np.abs(want).astype(np.float32))
+    assert np.all(np.abs(got - want) <= 2 * ulp + 1e-6)
+
+
+def test_tables_full_size_sampled_nodes():
+    w = W.voxel_survey()
+    grid, faces = voxel_model(w)
+    torch.cuda.synchronize()
+    g = grid.cpu().numpy()
+    want_grid = oracle.grf_density(w.grid_seed, *w.grid_shape, sigma_vox=w.grid_sigma_vox, amp=w.grid_amp)
+    assert np.array_equal(g, want_grid) or np.max(np.abs(g - want_grid) / np.spacing(np.abs(want_grid))) <= 2
+    f = faces.cpu().numpy()
+    nu, nv = w.table_n
+    rng = np.random.default_rng(1)
+    fi = np.repeat(np.arange(6), 4)
+    iu = np.array([v for _ in range(6) for v in (0, nu - 1, *rng.integers(0, nu, 2))])
+    iv = np.array([v for _ in range(6) for v in (nv - 1, 0, *rng.integers(0, nv, 2))])
+    spec = oracle_spec(w.with_(g_kind="zero"), grid=g)
+    want = oracle.table_nodes(spec, fi, iu, iv, nu, nv, threads=THREADS)
+    got = f[fi, iv, iu].astype(np.float64)
+    rel = np.abs(got - want) / np.abs(want)
+    assert np.all(rel < 2e-5), rel.max()
+
+
+def test_tables_all_exact_small_grid():
+    """With the near zone covering every voxel the tables are the exact sum."""
+    w = W.voxel_survey(shape=(16, 12, 8), table_n=(9, 7))
+    grid = torch.from_numpy(oracle.grf_density(3, 16, 12, 8, sigma_vox=1.5, amp=300.0)).cuda()
+    nu, nv = w.table_n
+    faces = torch.empty((6, nv, nu), dtype=torch.float32, device="cuda")
+    M.mcg_boundary_tables(M.problem(w.with_(g_kind="zero"), grid=grid), nu, nv, 1e6, faces)
+    torch.cuda.synchronize()
+    f = faces.cpu().numpy()
+    fi, iu, iv = np.meshgrid(np.arange(6), np.arange(nu), np.arange(nv), indexing="ij")
+    spec = oracle_spec(w.with_(g_kind="zero"), grid=grid.cpu().numpy())
+    want = oracle.table_nodes(spec, fi.ravel(), iu.ravel(), iv.ravel(), nu, nv, threads=THREADS)
+    got = f[fi.ravel(), iv.ravel(), iu.ravel()].astype(np.float64)
+    np.testing.assert_allclose(got, want, rtol=3e-7)
+
+
+@pytest.fixture(scope="module")
+def voxel_inputs():
+    w = W.voxel_survey(paths=512)
+    grid = oracle.grf_density(w.grid_seed, *w.grid_shape, sigma_vox=w.grid_sigma_vox, amp=w.grid_amp)
+    faces = smooth_tables(w, scale=-1e-4)
+    return w, grid, faces
+
+
+def test_voxel_walk_fp64_per_path(voxel_inputs):
+    w, grid, faces = voxel_inputs
+    st = w.stations[[0, 17, 100, 255]]
+    wg = w.with_(stations=st, paths=48)
+    ds = DeviceSolve(wg, precision=M.MCG_FP64, grid=torch.from_numpy(grid).cuda(),
+                     faces=torch.from_numpy(faces).cuda())
+    ds.reset()
+    ds.walk(1000)
+    u, d, steps = ds.per_path()
+    assert int(ds.status[0].item()) == 0
+    ref = oracle.solve(oracle_spec(wg, grid=grid, faces=faces), st, 48, p0=1000, per_path=True, threads=THREADS)
+    same = steps == ref.pp_steps
+    assert same.mean() >= 0.99
+    assert np.all(np.abs(u - ref.pp_u)[same] <= 1e-12 * np.abs(ref.pp_u)[same])
+    assert np.all(np.abs(d - ref.pp_d)[same] <= 1e-12 * np.abs(ref.pp_u)[same] / w.h)
+
+
+def test_voxel_walk_mixed_paired(voxel_inputs):
+    w, grid, faces = voxel_inputs
+    st = w.stations[[3, 60, 130, 250]]
+    wg = w.with_(stations=st, paths=512)
+    ds = DeviceSolve(wg, precision=M.MCG_MIXED, grid=torch.from_numpy(grid).cuda(),
+                     faces=torch.from_numpy(faces).cuda())
+    ds.reset()
+    ds.walk(0)
+    u, d, steps = ds.per_path()
+    assert int(ds.status[0].item()) == 0
+    ref = oracle.solve(oracle_spec(wg, grid=grid, faces=faces, ubits=23), st, 512, per_path=True, threads=THREADS)
+    assert (steps == ref.pp_steps).mean() > 0.9
+    for s in range(st.shape[0]):
+        diff = u[s] - ref.pp_u[s]
+        se = diff.std(ddof=1) / math.sqrt(diff.size)
+        um = abs(ref.pp_u[s].mean())
+        assert abs(diff.mean()) <= 4 * se + 1e-6 * um, (s, diff.mean(), se)
