@@ -258,6 +258,16 @@ def run_ours(args):
     for j in range(args.warmup, n_steps):
         issue(j)
     streams[0].wait_event(ev["end"][n_steps - 1])
+    if world > 1:
+        # the one exchange of a path-sharded solve: all-gather the station
+        # states and merge them in rank order (Chan's formula), then finalize
+        import torch.distributed as dist
+        with torch.cuda.stream(streams[0]):
+            gathered = [torch.empty_like(states) for _ in range(world)]
+            dist.all_gather(gathered, states)
+            parts = torch.stack(gathered).view(world, S, M.STATE_BYTES // 8).cpu().numpy()
+            merged = torch.from_numpy(M.mcg_states_merge(parts).reshape(-1)).to(dev)
+            M.mcg_finalize(merged, S, res[0], res[1], res[2], res[3], res[4], res[5], streams[0])
     t_end.record(streams[0])
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -265,7 +275,8 @@ def run_ours(args):
     elapsed_ms = t_start.elapsed_time(t_end)
 
     r = res.cpu().numpy()
-    path_steps_local = float(r[5].view(np.int64).sum())
+    # this rank's own path-steps (the steps field of its station states)
+    path_steps_local = float(states.view(S, M.STATE_BYTES // 8)[:, 5].sum().item())
     st_code = int(status[0].item())
     walk_ms = [ev["walk0"][j].elapsed_time(ev["walk1"][j]) for j in range(args.warmup, n_steps)]
     lat_ms = [ev["start"][j].elapsed_time(ev["end"][j]) for j in range(args.warmup, n_steps)]

@@ -238,6 +238,17 @@ MCG_API int mcg_reduce(const double* pp_u, const double* pp_d, const int64_t* pp
 MCG_API int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double* u, double* gz, double* se_u,
                  double* se_gz, int64_t* n_paths, int64_t* path_steps, void* stream);
 
+/* mcg_states_merge: the multi-GPU exchange step.  A solve whose paths are
+ * sharded over R ranks (each rank reducing its own path ranges with
+ * mcg_reduce) combines the ranks' station states here: out[s] = Chan merge
+ * of parts[0][s], parts[1][s], ..., parts[R-1][s] in that order (the same
+ * parallel-variance combination mcg_reduce applies batch after batch), so
+ * the result is deterministic for a fixed rank order and partition.
+ * The paper gathers per-GPU partial means on one node (Sec. 4).
+ *   parts: HOST, R x S states (rank-major).  out: HOST, S states (may alias
+ *   parts[0 .. S-1]).  States with n = 0 are skipped.  Allocates nothing. */
+MCG_API int mcg_states_merge(const mcg_station_state* parts, int64_t R, int64_t S, mcg_station_state* out);
+
 /* Bytes of device workspace mcgrav_solve uses for S stations and batches of
  * `batch` paths per station. */
 MCG_API size_t mcg_workspace_bytes(int64_t S, int64_t batch);

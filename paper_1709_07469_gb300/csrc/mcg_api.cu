@@ -441,6 +441,35 @@ int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblo
     return e == cudaSuccess ? MCG_OK : cuda_fail(e, "normals kernel launch");
 }
 
+int mcg_states_merge(const mcg_station_state* parts, int64_t R, int64_t S, mcg_station_state* out)
+{
+    if (R < 0 || S < 0) return set_error(MCG_ERR_ARG, "R and S must be non-negative");
+    if (R == 0 || S == 0) return MCG_OK;
+    if (!parts || !out) return set_error(MCG_ERR_ARG, "null states");
+    for (int64_t s = 0; s < S; ++s) {
+        mcg_station_state a;
+        std::memset(&a, 0, sizeof(a));
+        for (int64_t r = 0; r < R; ++r) {
+            const mcg_station_state& b = parts[r * S + s];
+            if (!(b.n > 0.0)) continue;
+            if (a.n == 0.0) {
+                a = b;
+                continue;
+            }
+            const double n = a.n + b.n;
+            const double du = b.mean_u - a.mean_u, dd = b.mean_d - a.mean_d;
+            a.mean_u = a.mean_u + du * (b.n / n);
+            a.m2_u = a.m2_u + b.m2_u + du * du * (a.n * b.n / n);
+            a.mean_d = a.mean_d + dd * (b.n / n);
+            a.m2_d = a.m2_d + b.m2_d + dd * dd * (a.n * b.n / n);
+            a.steps = a.steps + b.steps;
+            a.n = n;
+        }
+        out[s] = a;
+    }
+    return MCG_OK;
+}
+
 size_t mcg_grf_work_bytes(int64_t nx, int64_t ny, int64_t nz)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0) return 0;

@@ -102,6 +102,8 @@ def load(path: str | None = None):
     lib.mcg_walk_static.restype = C.c_int
     lib.mcg_walk_static_max_items.argtypes = []
     lib.mcg_walk_static_max_items.restype = C.c_int64
+    lib.mcg_states_merge.argtypes = [vp, i64, i64, vp]
+    lib.mcg_states_merge.restype = C.c_int
     lib.mcg_grf_work_bytes.argtypes = [i64, i64, i64]
     lib.mcg_grf_work_bytes.restype = C.c_size_t
     lib.mcg_grf_density.argtypes = [u64, i64, i64, i64, d, d, vp, vp, vp]
@@ -297,3 +299,16 @@ def mcg_grf_density(seed: int, nx: int, ny: int, nz: int, sigma_vox: float, amp:
 def mcg_boundary_tables(prob: Problem, nu: int, nv: int, near_cells: float, faces_out, stream=None) -> int:
     return _check(load().mcg_boundary_tables(C.byref(prob.domain), C.byref(prob.density), nu, nv, near_cells,
                                              _ptr(faces_out), _stream_handle(stream)))
+
+
+STATE_FIELDS = ("n", "mean_u", "m2_u", "mean_d", "m2_d", "steps")
+
+
+def mcg_states_merge(parts: np.ndarray) -> np.ndarray:
+    """Merge per-rank station states (float64 array [R, S, 8]) in rank order."""
+    p = np.ascontiguousarray(parts, dtype=np.float64)
+    if p.ndim != 3 or p.shape[2] != STATE_BYTES // 8:
+        raise ValueError("parts must be [R, S, 8] float64")
+    out = np.zeros(p.shape[1:], dtype=np.float64)
+    _check(load().mcg_states_merge(p.ctypes.data, p.shape[0], p.shape[1], out.ctypes.data))
+    return out
