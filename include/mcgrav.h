@@ -270,6 +270,74 @@ MCG_API int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int6
                 void* out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of solve requests.                          */
+/* ---------------------------------------------------------------------- */
+/* An inversion code calls the forward solver many times with different
+ * station sets, models and accuracy targets (the paper's motivation, Sec. 1).
+ * The server keeps models resident on the device, admits requests while
+ * their buffers fit an HBM budget, and advances every admitted request in
+ * rounds: one round walks `chunk_paths` more paths (path indices k*chunk ..
+ * (k+1)*chunk - 1 of each station for round k) and merges them into the
+ * request's station statistics; after each round the request stops once
+ * every station reaches its relative standard error target (and has at
+ * least min_paths paths) or max_paths.  Rounds of different requests run on
+ * a pool of streams and overlap on the GPU; a request's result depends only
+ * on its own (seed, stations, target), never on what else is in flight.
+ * All calls are thread-safe.  Objects are owned by the library until the
+ * matching destroy / free call. */
+typedef struct mcg_model mcg_model;
+typedef struct mcg_server mcg_server;
+typedef struct mcg_request mcg_request;
+
+typedef struct {
+    int32_t streams;          /* stream pool size (default 8)                       */
+    int32_t max_active;       /* requests in flight at most (default 64)             */
+    int64_t hbm_budget;       /* bytes of request buffers in flight (default 8 GiB)  */
+    int64_t chunk_paths;      /* paths per station per round (default 4096)          */
+    int64_t min_paths;        /* paths per station before the target is checked (default 2 chunks) */
+    int64_t max_paths;        /* cap per station (default 10^7)                      */
+    mcg_options walk;         /* walk options (precision, h, sigma, clip, crn_gz, block, max_steps) */
+} mcg_server_config;
+
+MCG_API void mcg_server_config_default(mcg_server_config* c);
+
+/* mcg_model_create: a device-resident copy of the problem (domain, density,
+ * boundary data, time step dt and g_z difference step h; the server's walk
+ * options supply the rest).  Grid and faces may be host or device pointers;
+ * they are copied, so the caller may free its buffers afterwards.
+ * Blocking. */
+MCG_API int mcg_model_create(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+                             double dt, double h, mcg_model** out);
+MCG_API int mcg_model_destroy(mcg_model* m);
+
+/* mcg_server_create: starts the scheduler thread on the current device. */
+MCG_API int mcg_server_create(const mcg_server_config* cfg, mcg_server** out);
+/* mcg_server_destroy: cancels nothing; waits for every admitted and queued
+ * request to finish, then stops the thread.  Requests stay valid until
+ * freed. */
+MCG_API int mcg_server_destroy(mcg_server* s);
+
+/* mcg_submit: queues a request (non-blocking).  stations: HOST, S x 3
+ * (copied).  target_rel_se: stop when se_u <= target |u| at every station.
+ * The model must outlive the request. */
+MCG_API int mcg_submit(mcg_server* s, const mcg_model* m, const double* stations, int64_t S, double target_rel_se,
+                       uint64_t seed, mcg_request** out);
+/* mcg_poll: *done = 1 and the HOST result arrays (length S) filled once the
+ * request finished; returns the request's status then (MCG_OK, or the error
+ * that ended it).  Non-blocking. */
+MCG_API int mcg_poll(mcg_request* r, mcg_result* out, int* done);
+/* mcg_wait: blocks until the request finished (at most timeout_ms, < 0 =
+ * forever; MCG_ERR_TIMEOUT when the wait gives up), then as mcg_poll. */
+MCG_API int mcg_wait(mcg_request* r, mcg_result* out, int64_t timeout_ms);
+/* mcg_cancel: stops scheduling rounds of the request; it finishes with
+ * MCG_ERR_CANCELLED and partial statistics. */
+MCG_API int mcg_cancel(mcg_request* r);
+/* mcg_request_info: paths per station done, rounds, latency in seconds from
+ * submit to completion (or so far).  Any pointer may be NULL. */
+MCG_API int mcg_request_info(const mcg_request* r, int64_t* paths, int64_t* rounds, double* seconds);
+MCG_API int mcg_request_free(mcg_request* r);
+
+/* ---------------------------------------------------------------------- */
 /* Heterogeneous model set-up (once per model, outside the walk).            */
 /* ---------------------------------------------------------------------- */
 

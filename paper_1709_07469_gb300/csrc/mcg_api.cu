@@ -20,8 +20,6 @@ thread_local char g_err[512] = "";
 
 constexpr double kPi = 3.14159265358979323846;
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
 int cuda_fail(cudaError_t e, const char* what)
@@ -39,8 +37,6 @@ int set_error(int code, const char* fmt, ...)
     va_end(ap);
     return code;
 }
-
-namespace {
 
 // Checks the problem description and fills the launch parameters (without
 // the work list, which the caller adds).
@@ -177,7 +173,6 @@ int status_from_bits(int bits)
     return MCG_OK;
 }
 
-}  // namespace
 }  // namespace mcg
 
 // ---------------------------------------------------------------------------

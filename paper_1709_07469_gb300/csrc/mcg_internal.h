@@ -77,4 +77,11 @@ int boundary_tables(const mcg_domain* d, const mcg_density* rho, int32_t nu, int
 // Thread-local error message (mcg_api.cu).
 int set_error(int code, const char* fmt, ...);
 
+// Argument checks shared by the entry points (mcg_api.cu).
+int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B, double dt, uint64_t seed,
+                const mcg_options* o, WalkParams& P);
+int check_station(const WalkParams& P, const double* x, int64_t s);
+int status_from_bits(int bits);
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 }  // namespace mcg

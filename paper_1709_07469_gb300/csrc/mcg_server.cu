@@ -1,0 +1,561 @@
+// mcg_server.cu -- continuous batching of solve requests (host runtime).
+//
+// A scheduler thread admits queued requests while their device buffers fit
+// the HBM budget, and advances every admitted request round by round on a
+// pool of CUDA streams: each round walks `chunk_paths` more paths of each of
+// the request's stations (round k takes path indices k*chunk ..
+// (k+1)*chunk-1), reduces them into the request's station statistics,
+// finalizes and copies u, g_z, standard errors and path counts into pinned
+// host memory.  When a round's event has completed the thread decides on
+// the host whether the request reached its target; if not, it launches the
+// next round.  Rounds of different requests overlap on the GPU, so one
+// request's exit-time tail runs beside other requests' walks.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mcg_internal.h"
+#include "mcgrav.h"
+
+using namespace mcg;
+using Clock = std::chrono::steady_clock;
+
+struct mcg_model {
+    mcg_domain dom;
+    mcg_density den;
+    mcg_boundary bnd;
+    double dt = 0.0;
+    double h = 0.0;
+    float* grid = nullptr;   // owned device copy
+    float* faces = nullptr;  // owned device copy
+};
+
+struct mcg_request {
+    mcg_server* server = nullptr;
+    const mcg_model* model = nullptr;
+    std::vector<double> stations;
+    int64_t S = 0;
+    double target = 0.0;
+    uint64_t seed = 0;
+    // scheduler-thread state
+    WalkParams P;
+    int stream = -1;
+    char* dev = nullptr;
+    size_t bytes = 0;
+    int64_t round = 0;
+    bool in_flight = false;
+    cudaEvent_t ev = nullptr;
+    double* h_res = nullptr;  // pinned: 6 S doubles + status word
+    // published state
+    std::mutex mu;
+    std::condition_variable cv;
+    bool done = false;
+    int status = MCG_OK;
+    std::string message;
+    std::vector<double> res;  // 6 S: u, gz, se_u, se_gz, n (int64 bits), steps (int64 bits)
+    std::atomic<int64_t> paths{0};
+    std::atomic<int64_t> rounds{0};
+    std::atomic<bool> cancel{false};
+    Clock::time_point t_submit, t_done;
+};
+
+struct mcg_server {
+    mcg_server_config cfg;
+    int device = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> load;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<mcg_request*> pending;
+    bool stopping = false;
+    std::vector<mcg_request*> active;
+    size_t used = 0;
+    std::thread th;
+};
+
+namespace {
+
+// Device layout of a request: stations | states | status word + counter |
+// finalized results | per-path u, d, steps | walk scratch.
+struct Layout {
+    size_t st, states, status, res, u, d, steps, work, total;
+};
+
+Layout layout(int64_t S, int64_t chunk, int precision)
+{
+    Layout L;
+    const size_t s = (size_t)S, n = (size_t)S * (size_t)chunk;
+    size_t o = 0;
+    L.st = o;
+    o += align256(s * 3 * sizeof(double));
+    L.states = o;
+    o += align256(s * sizeof(mcg_station_state));
+    L.status = o;
+    o += 256;
+    L.res = o;
+    o += align256(s * 6 * sizeof(double));
+    L.u = o;
+    o += align256(n * sizeof(double));
+    L.d = o;
+    o += align256(n * sizeof(double));
+    L.steps = o;
+    o += align256(n * sizeof(int64_t));
+    L.work = o;
+    o += mcg_walk_work_bytes(S, chunk, precision);
+    L.total = o;
+    return L;
+}
+
+void finish(mcg_request* r, int status, const char* msg)
+{
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (r->h_res) r->res.assign(r->h_res, r->h_res + 6 * r->S);
+    r->status = status;
+    if (msg) r->message = msg;
+    r->t_done = Clock::now();
+    r->done = true;
+    r->cv.notify_all();
+}
+
+// Launches round r->round of the request on its stream.
+int launch_round(mcg_server* sv, mcg_request* r)
+{
+    const int64_t chunk = sv->cfg.chunk_paths;
+    const Layout L = layout(r->S, chunk, sv->cfg.walk.precision);
+    cudaStream_t st = sv->streams[r->stream];
+    WalkParams P = r->P;
+    P.stations = (const double*)(r->dev + L.st);
+    P.S = r->S;
+    P.N = chunk;
+    P.p0 = r->round * chunk;
+    P.total = (unsigned long long)r->S * (unsigned long long)chunk;
+    P.pp_u = (double*)(r->dev + L.u);
+    P.pp_d = (double*)(r->dev + L.d);
+    P.pp_steps = (int64_t*)(r->dev + L.steps);
+    P.status = (int32_t*)(r->dev + L.status);
+    P.counter = (unsigned long long*)(r->dev + L.status + 128);
+    if (sv->cfg.walk.precision == MCG_MIXED) {
+        const size_t n = (size_t)P.total;
+        P.frec = (float*)(r->dev + L.work);
+        P.drec = (double*)(r->dev + L.work + align256(n * 3 * 8 * sizeof(float)));
+    }
+    mcg_station_state* states = (mcg_station_state*)(r->dev + L.states);
+    double* res = (double*)(r->dev + L.res);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st)) ||
+        (e = launch_walk(P, sv->cfg.walk.precision, sv->cfg.walk.block ? sv->cfg.walk.block : 128, st)) ||
+        (e = launch_reduce(P.pp_u, P.pp_d, P.pp_steps, r->S, chunk, states, st)) ||
+        (e = launch_finalize(states, r->S, res, res + r->S, res + 2 * r->S, res + 3 * r->S, (int64_t*)(res + 4 * r->S),
+                             (int64_t*)(res + 5 * r->S), st)) ||
+        (e = cudaMemcpyAsync(r->h_res, res, 6 * r->S * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(r->h_res + 6 * r->S, P.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaEventRecord(r->ev, st)))
+        return set_error(MCG_ERR_CUDA, "round launch: %s", cudaGetErrorString(e));
+    r->in_flight = true;
+    return MCG_OK;
+}
+
+int admit(mcg_server* sv, mcg_request* r)
+{
+    int best = 0;
+    for (int i = 1; i < (int)sv->streams.size(); ++i)
+        if (sv->load[i] < sv->load[best]) best = i;
+    r->stream = best;
+    cudaStream_t st = sv->streams[best];
+    const Layout L = layout(r->S, sv->cfg.chunk_paths, sv->cfg.walk.precision);
+    cudaError_t e = cudaMallocAsync((void**)&r->dev, L.total, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        r->dev = nullptr;
+        return MCG_ERR_OOM;
+    }
+    r->bytes = L.total;
+    if ((e = cudaMemcpyAsync(r->dev + L.st, r->stations.data(), r->S * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                             st)) ||
+        (e = cudaMemsetAsync(r->dev + L.states, 0, r->S * sizeof(mcg_station_state), st)) ||
+        (e = cudaMemsetAsync(r->dev + L.status, 0, 256, st))) {
+        cudaFreeAsync(r->dev, st);
+        r->dev = nullptr;
+        return MCG_ERR_CUDA;
+    }
+    sv->load[best]++;
+    sv->used += L.total;
+    return MCG_OK;
+}
+
+void release(mcg_server* sv, mcg_request* r)
+{
+    if (r->dev) {
+        cudaFreeAsync(r->dev, sv->streams[r->stream]);
+        r->dev = nullptr;
+        sv->used -= r->bytes;
+        sv->load[r->stream]--;
+    }
+}
+
+// The request reached its end after the round whose results are in h_res?
+bool reached(const mcg_server* sv, const mcg_request* r, int64_t n)
+{
+    if (n >= sv->cfg.max_paths) return true;
+    if (n < sv->cfg.min_paths) return false;
+    for (int64_t s = 0; s < r->S; ++s) {
+        const double u = r->h_res[s], se = r->h_res[2 * r->S + s];
+        if (!(se <= r->target * std::fabs(u))) return false;
+    }
+    return true;
+}
+
+void scheduler(mcg_server* sv)
+{
+    cudaSetDevice(sv->device);
+    for (;;) {
+        bool progressed = false;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            if (sv->stopping && sv->pending.empty() && sv->active.empty()) break;
+            // admission: FIFO, while the budget and the slot count allow
+            while (!sv->pending.empty() && (int)sv->active.size() < sv->cfg.max_active) {
+                mcg_request* r = sv->pending.front();
+                const Layout L = layout(r->S, sv->cfg.chunk_paths, sv->cfg.walk.precision);
+                if (!sv->active.empty() && sv->used + L.total > (size_t)sv->cfg.hbm_budget) break;
+                sv->pending.pop_front();
+                lk.unlock();
+                const int rc = admit(sv, r);
+                lk.lock();
+                if (rc == MCG_OK) {
+                    sv->active.push_back(r);
+                } else if (rc == MCG_ERR_OOM && !sv->active.empty()) {
+                    sv->pending.push_front(r);  // retry when memory frees up
+                    break;
+                } else {
+                    finish(r, rc, "admission failed");
+                }
+                progressed = true;
+            }
+        }
+        // advance the admitted requests
+        std::vector<mcg_request*> act;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            act = sv->active;
+        }
+        // After finish() the caller may free the request at any moment: the
+        // loop below never touches `r` again once it has been finished.
+        auto retire = [sv](mcg_request* r) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (size_t i = 0; i < sv->active.size(); ++i)
+                if (sv->active[i] == r) {
+                    sv->active.erase(sv->active.begin() + i);
+                    break;
+                }
+        };
+        for (mcg_request* r : act) {
+            if (r->in_flight) {
+                const cudaError_t q = cudaEventQuery(r->ev);
+                if (q == cudaErrorNotReady) continue;
+                r->in_flight = false;
+                progressed = true;
+                int end = -1;  // status that ends the request, -1: continue
+                const char* msg = nullptr;
+                if (q != cudaSuccess) {
+                    end = MCG_ERR_CUDA;
+                    msg = cudaGetErrorString(q);
+                } else {
+                    r->round++;
+                    r->rounds.store(r->round);
+                    int64_t n = 0;
+                    std::memcpy(&n, r->h_res + 4 * r->S, sizeof(int64_t));
+                    r->paths.store(n);
+                    int32_t bits = 0;
+                    std::memcpy(&bits, r->h_res + 6 * r->S, sizeof(int32_t));
+                    if (bits) {
+                        end = status_from_bits(bits);
+                        msg = "walk status";
+                    } else if (r->cancel.load()) {
+                        end = MCG_ERR_CANCELLED;
+                        msg = "cancelled";
+                    } else if (reached(sv, r, n)) {
+                        end = MCG_OK;
+                    }
+                }
+                if (end >= 0) {
+                    release(sv, r);
+                    retire(r);
+                    finish(r, end, msg);
+                    continue;
+                }
+            }
+            if (r->cancel.load() && r->round > 0) {
+                release(sv, r);
+                retire(r);
+                finish(r, MCG_ERR_CANCELLED, "cancelled");
+                continue;
+            }
+            if (launch_round(sv, r) != MCG_OK) {
+                release(sv, r);
+                retire(r);
+                finish(r, MCG_ERR_CUDA, "round launch failed");
+                continue;
+            }
+            progressed = true;
+        }
+        if (!progressed) {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void mcg_server_config_default(mcg_server_config* c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->streams = 8;
+    c->max_active = 64;
+    c->hbm_budget = (int64_t)8 << 30;
+    c->chunk_paths = 4096;
+    c->min_paths = 2 * 4096;
+    c->max_paths = 10000000;
+    mcg_options_default(&c->walk);
+}
+
+int mcg_model_create(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary, double dt,
+                     double h, mcg_model** out)
+{
+    if (!out) return set_error(MCG_ERR_ARG, "null output");
+    *out = nullptr;
+    mcg_options o;
+    mcg_options_default(&o);
+    o.h = h;
+    WalkParams P;
+    int rc = make_params(domain, density, boundary, dt, 0, &o, P);
+    if (rc) return rc;
+    mcg_model* m = new mcg_model();
+    m->dom = *domain;
+    m->den = *density;
+    m->bnd = *boundary;
+    m->dt = dt;
+    m->h = h;
+    cudaError_t e = cudaSuccess;
+    if (density->kind == MCG_RHO_VOXEL) {
+        const size_t n = (size_t)density->nx * density->ny * density->nz;
+        if ((e = cudaMalloc(&m->grid, n * sizeof(float))) ||
+            (e = cudaMemcpy(m->grid, density->grid, n * sizeof(float), cudaMemcpyDefault))) {
+            mcg_model_destroy(m);
+            return set_error(e == cudaErrorMemoryAllocation ? MCG_ERR_OOM : MCG_ERR_CUDA, "model grid: %s",
+                             cudaGetErrorString(e));
+        }
+        m->den.grid = m->grid;
+    }
+    if (boundary->kind == MCG_G_TABLE) {
+        const size_t n = (size_t)6 * boundary->nu * boundary->nv;
+        if ((e = cudaMalloc(&m->faces, n * sizeof(float))) ||
+            (e = cudaMemcpy(m->faces, boundary->faces, n * sizeof(float), cudaMemcpyDefault))) {
+            mcg_model_destroy(m);
+            return set_error(e == cudaErrorMemoryAllocation ? MCG_ERR_OOM : MCG_ERR_CUDA, "model faces: %s",
+                             cudaGetErrorString(e));
+        }
+        m->bnd.faces = m->faces;
+    }
+    *out = m;
+    return MCG_OK;
+}
+
+int mcg_model_destroy(mcg_model* m)
+{
+    if (!m) return MCG_OK;
+    if (m->grid) cudaFree(m->grid);
+    if (m->faces) cudaFree(m->faces);
+    delete m;
+    return MCG_OK;
+}
+
+int mcg_server_create(const mcg_server_config* cfg_in, mcg_server** out)
+{
+    if (!out) return set_error(MCG_ERR_ARG, "null output");
+    *out = nullptr;
+    mcg_server_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else mcg_server_config_default(&cfg);
+    if (cfg.streams <= 0 || cfg.streams > 64) return set_error(MCG_ERR_ARG, "streams must be in [1, 64]");
+    if (cfg.max_active <= 0) return set_error(MCG_ERR_ARG, "max_active must be positive");
+    if (cfg.chunk_paths <= 0 || cfg.max_paths < cfg.chunk_paths || cfg.hbm_budget <= 0)
+        return set_error(MCG_ERR_ARG, "need chunk_paths > 0, max_paths >= chunk_paths, hbm_budget > 0");
+    if (cfg.walk.precision != MCG_FP64 && cfg.walk.precision != MCG_MIXED)
+        return set_error(MCG_ERR_ARG, "walk.precision must be MCG_FP64 or MCG_MIXED");
+    mcg_server* sv = new mcg_server();
+    sv->cfg = cfg;
+    cudaGetDevice(&sv->device);
+    // keep freed request buffers in the stream-ordered pool (up to the
+    // budget) instead of returning them to the driver after every request
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) {
+        uint64_t thr = (uint64_t)cfg.hbm_budget;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    for (int i = 0; i < cfg.streams; ++i) {
+        cudaStream_t st;
+        const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (cudaStream_t s2 : sv->streams) cudaStreamDestroy(s2);
+            delete sv;
+            return set_error(MCG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        sv->streams.push_back(st);
+        sv->load.push_back(0);
+    }
+    sv->th = std::thread(scheduler, sv);
+    *out = sv;
+    return MCG_OK;
+}
+
+int mcg_server_destroy(mcg_server* sv)
+{
+    if (!sv) return MCG_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stopping = true;
+    }
+    sv->cv.notify_all();
+    sv->th.join();
+    for (cudaStream_t st : sv->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    delete sv;
+    return MCG_OK;
+}
+
+int mcg_submit(mcg_server* sv, const mcg_model* m, const double* stations, int64_t S, double target_rel_se,
+               uint64_t seed, mcg_request** out)
+{
+    if (!sv || !m || !out) return set_error(MCG_ERR_ARG, "null server/model/output");
+    *out = nullptr;
+    if (S <= 0 || !stations) return set_error(MCG_ERR_ARG, "need S >= 1 stations");
+    if (S > (int64_t)1 << 32) return set_error(MCG_ERR_ARG, "too many stations");
+    if (!(target_rel_se > 0.0)) return set_error(MCG_ERR_ARG, "target_rel_se must be positive");
+    mcg_request* r = new mcg_request();
+    mcg_options o = sv->cfg.walk;
+    o.h = m->h;
+    int rc = make_params(&m->dom, &m->den, &m->bnd, m->dt, seed, &o, r->P);
+    for (int64_t s = 0; rc == MCG_OK && s < S; ++s) rc = check_station(r->P, stations + 3 * s, s);
+    if (rc) {
+        delete r;
+        return rc;
+    }
+    r->server = sv;
+    r->model = m;
+    r->stations.assign(stations, stations + 3 * S);
+    r->S = S;
+    r->target = target_rel_se;
+    r->seed = seed;
+    cudaError_t e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_res, (6 * S + 1) * sizeof(double));
+    if (e != cudaSuccess) {
+        if (r->ev) cudaEventDestroy(r->ev);
+        delete r;
+        return set_error(MCG_ERR_CUDA, "request set-up: %s", cudaGetErrorString(e));
+    }
+    std::memset(r->h_res, 0, (6 * S + 1) * sizeof(double));
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stopping) {
+            cudaFreeHost(r->h_res);
+            cudaEventDestroy(r->ev);
+            delete r;
+            return set_error(MCG_ERR_ARG, "server is stopping");
+        }
+        sv->pending.push_back(r);
+    }
+    sv->cv.notify_all();
+    *out = r;
+    return MCG_OK;
+}
+
+static void copy_result(const mcg_request* r, mcg_result* out)
+{
+    if (!out) return;
+    const int64_t S = r->S;
+    for (int64_t s = 0; s < S; ++s) {
+        if (out->u) out->u[s] = r->res[s];
+        if (out->gz) out->gz[s] = r->res[S + s];
+        if (out->se_u) out->se_u[s] = r->res[2 * S + s];
+        if (out->se_gz) out->se_gz[s] = r->res[3 * S + s];
+        if (out->n_paths) std::memcpy(&out->n_paths[s], &r->res[4 * S + s], sizeof(int64_t));
+        if (out->path_steps) std::memcpy(&out->path_steps[s], &r->res[5 * S + s], sizeof(int64_t));
+    }
+}
+
+int mcg_poll(mcg_request* r, mcg_result* out, int* done)
+{
+    if (!r || !done) return set_error(MCG_ERR_ARG, "null request/done");
+    std::lock_guard<std::mutex> lk(r->mu);
+    *done = r->done ? 1 : 0;
+    if (!r->done) return MCG_OK;
+    copy_result(r, out);
+    if (r->status) set_error(r->status, "%s", r->message.c_str());
+    return r->status;
+}
+
+int mcg_wait(mcg_request* r, mcg_result* out, int64_t timeout_ms)
+{
+    if (!r) return set_error(MCG_ERR_ARG, "null request");
+    std::unique_lock<std::mutex> lk(r->mu);
+    if (timeout_ms < 0) r->cv.wait(lk, [&] { return r->done; });
+    else if (!r->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; }))
+        return set_error(MCG_ERR_TIMEOUT, "request not finished within %lld ms", (long long)timeout_ms);
+    copy_result(r, out);
+    if (r->status) set_error(r->status, "%s", r->message.c_str());
+    return r->status;
+}
+
+int mcg_cancel(mcg_request* r)
+{
+    if (!r) return set_error(MCG_ERR_ARG, "null request");
+    r->cancel.store(true);
+    if (r->server) r->server->cv.notify_all();
+    return MCG_OK;
+}
+
+int mcg_request_info(const mcg_request* r, int64_t* paths, int64_t* rounds, double* seconds)
+{
+    if (!r) return set_error(MCG_ERR_ARG, "null request");
+    if (paths) *paths = r->paths.load();
+    if (rounds) *rounds = r->rounds.load();
+    if (seconds) {
+        mcg_request* rr = const_cast<mcg_request*>(r);
+        std::lock_guard<std::mutex> lk(rr->mu);
+        const Clock::time_point t = r->done ? r->t_done : Clock::now();
+        *seconds = std::chrono::duration<double>(t - r->t_submit).count();
+    }
+    return MCG_OK;
+}
+
+int mcg_request_free(mcg_request* r)
+{
+    if (!r) return MCG_OK;
+    {
+        std::unique_lock<std::mutex> lk(r->mu);
+        if (!r->done) return set_error(MCG_ERR_ARG, "request still running (cancel and wait first)");
+    }
+    if (r->h_res) cudaFreeHost(r->h_res);
+    if (r->ev) cudaEventDestroy(r->ev);
+    delete r;
+    return MCG_OK;
+}
+
+}  // extern "C"

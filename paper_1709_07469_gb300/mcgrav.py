@@ -53,6 +53,12 @@ class mcg_result(C.Structure):
                 ("n_paths", C.c_void_p), ("path_steps", C.c_void_p)]
 
 
+class mcg_server_config(C.Structure):
+    _fields_ = [("streams", C.c_int32), ("max_active", C.c_int32), ("hbm_budget", C.c_int64),
+                ("chunk_paths", C.c_int64), ("min_paths", C.c_int64), ("max_paths", C.c_int64),
+                ("walk", mcg_options)]
+
+
 class mcg_station_state(C.Structure):
     _fields_ = [("n", C.c_double), ("mean_u", C.c_double), ("m2_u", C.c_double), ("mean_d", C.c_double),
                 ("m2_d", C.c_double), ("steps", C.c_double), ("pad", C.c_double * 2)]
@@ -104,6 +110,28 @@ def load(path: str | None = None):
     lib.mcg_walk_static_max_items.restype = C.c_int64
     lib.mcg_states_merge.argtypes = [vp, i64, i64, vp]
     lib.mcg_states_merge.restype = C.c_int
+    lib.mcg_server_config_default.argtypes = [P(mcg_server_config)]
+    lib.mcg_server_config_default.restype = None
+    lib.mcg_model_create.argtypes = [P(mcg_domain), P(mcg_density), P(mcg_boundary), d, d, P(vp)]
+    lib.mcg_model_create.restype = C.c_int
+    lib.mcg_model_destroy.argtypes = [vp]
+    lib.mcg_model_destroy.restype = C.c_int
+    lib.mcg_server_create.argtypes = [P(mcg_server_config), P(vp)]
+    lib.mcg_server_create.restype = C.c_int
+    lib.mcg_server_destroy.argtypes = [vp]
+    lib.mcg_server_destroy.restype = C.c_int
+    lib.mcg_submit.argtypes = [vp, vp, vp, i64, d, u64, P(vp)]
+    lib.mcg_submit.restype = C.c_int
+    lib.mcg_poll.argtypes = [vp, P(mcg_result), P(C.c_int)]
+    lib.mcg_poll.restype = C.c_int
+    lib.mcg_wait.argtypes = [vp, P(mcg_result), i64]
+    lib.mcg_wait.restype = C.c_int
+    lib.mcg_cancel.argtypes = [vp]
+    lib.mcg_cancel.restype = C.c_int
+    lib.mcg_request_info.argtypes = [vp, P(i64), P(i64), P(d)]
+    lib.mcg_request_info.restype = C.c_int
+    lib.mcg_request_free.argtypes = [vp]
+    lib.mcg_request_free.restype = C.c_int
     lib.mcg_grf_work_bytes.argtypes = [i64, i64, i64]
     lib.mcg_grf_work_bytes.restype = C.c_size_t
     lib.mcg_grf_density.argtypes = [u64, i64, i64, i64, d, d, vp, vp, vp]
@@ -312,3 +340,81 @@ def mcg_states_merge(parts: np.ndarray) -> np.ndarray:
     out = np.zeros(p.shape[1:], dtype=np.float64)
     _check(load().mcg_states_merge(p.ctypes.data, p.shape[0], p.shape[1], out.ctypes.data))
     return out
+
+
+# --- serving --------------------------------------------------------------------
+
+def server_config(opts: mcg_options | None = None, **kw) -> mcg_server_config:
+    c = mcg_server_config()
+    load().mcg_server_config_default(C.byref(c))
+    if opts is not None:
+        c.walk = opts
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def mcg_model_create(prob: Problem, dt: float, h: float) -> int:
+    out = C.c_void_p()
+    _check(load().mcg_model_create(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary), dt, h,
+                                   C.byref(out)))
+    return out.value
+
+
+def mcg_model_destroy(model: int) -> int:
+    return _check(load().mcg_model_destroy(model))
+
+
+def mcg_server_create(cfg: mcg_server_config) -> int:
+    h = C.c_void_p()
+    _check(load().mcg_server_create(C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def mcg_server_destroy(server: int) -> int:
+    return _check(load().mcg_server_destroy(server))
+
+
+def mcg_submit(server: int, model: int, stations: np.ndarray, target_rel_se: float, seed: int) -> int:
+    st = np.ascontiguousarray(stations, dtype=np.float64).reshape(-1, 3)
+    h = C.c_void_p()
+    _check(load().mcg_submit(server, model, st.ctypes.data, st.shape[0], target_rel_se,
+                             seed & 0xFFFFFFFFFFFFFFFF, C.byref(h)))
+    return h.value
+
+
+def _result_buffers(S: int):
+    out = {k: np.full(S, np.nan) for k in ("u", "gz", "se_u", "se_gz")}
+    out["n_paths"] = np.zeros(S, dtype=np.int64)
+    out["path_steps"] = np.zeros(S, dtype=np.int64)
+    res = mcg_result(*[out[k].ctypes.data for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps")])
+    return out, res
+
+
+def mcg_poll(request: int, S: int):
+    """(done, status, result dict or None)."""
+    out, res = _result_buffers(S)
+    done = C.c_int(0)
+    rc = load().mcg_poll(request, C.byref(res), C.byref(done))
+    return bool(done.value), rc, (out if done.value else None)
+
+
+def mcg_wait(request: int, S: int, timeout_ms: int = -1):
+    """(status, result dict); MCG_ERR_TIMEOUT leaves the dict unfilled."""
+    out, res = _result_buffers(S)
+    rc = load().mcg_wait(request, C.byref(res), timeout_ms)
+    return rc, out
+
+
+def mcg_cancel(request: int) -> int:
+    return _check(load().mcg_cancel(request))
+
+
+def mcg_request_info(request: int):
+    paths, rounds, secs = C.c_int64(), C.c_int64(), C.c_double()
+    _check(load().mcg_request_info(request, C.byref(paths), C.byref(rounds), C.byref(secs)))
+    return paths.value, rounds.value, secs.value
+
+
+def mcg_request_free(request: int) -> int:
+    return _check(load().mcg_request_free(request))

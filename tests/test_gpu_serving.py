@@ -1,0 +1,145 @@
+"""Continuous batching (mcg_server_*): requests of different station counts,
+models and targets overlap on the GPU; each result must be the same alone and
+in the mix (bit for bit: a request's paths, chunks and merge order depend only
+on its own seed, stations and target), equal to the device-level solve with
+the same chunking, stop at its target, and honour cancellation and the HBM
+budget."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_07469_gb300 import build as B
+from paper_1709_07469_gb300 import mcgrav as M
+from paper_1709_07469_gb300 import workloads as W
+from paper_1709_07469_gb300.device import DeviceSolve
+from tests.helpers import smooth_tables
+
+pytestmark = pytest.mark.gpu
+CHUNK = 2048
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    B.build()
+    M.load()
+
+
+@pytest.fixture(scope="module")
+def models():
+    sph = W.sphere_line()
+    pri = W.prism_ore_body()
+    vox = W.voxel_survey(shape=(32, 32, 16), table_n=(33, 33))
+    grid = oracle.grf_density(1, 32, 32, 16, sigma_vox=2.0, amp=300.0)
+    faces = smooth_tables(vox, scale=-1e-4)
+    m = {"sphere": (sph, M.mcg_model_create(M.problem(sph), sph.dt, sph.h)),
+         "prism": (pri, M.mcg_model_create(M.problem(pri), pri.dt, pri.h)),
+         "voxel": (vox, M.mcg_model_create(M.problem(vox, grid=grid, faces=faces), vox.dt, vox.h))}
+    yield m
+    for _, h in m.values():
+        M.mcg_model_destroy(h)
+
+
+def server(w, **kw):
+    cfg = M.server_config(M.options(w), chunk_paths=CHUNK, min_paths=2 * CHUNK, **kw)
+    return M.mcg_server_create(cfg)
+
+
+def run_alone(w, model, stations, target, seed):
+    sv = server(w)
+    try:
+        rq = M.mcg_submit(sv, model, stations, target, seed)
+        rc, out = M.mcg_wait(rq, len(stations), 120_000)
+        info = M.mcg_request_info(rq)
+        M.mcg_request_free(rq)
+    finally:
+        M.mcg_server_destroy(sv)
+    assert rc == M.MCG_OK
+    return out, info
+
+
+def test_alone_equals_in_mix(models):
+    w, h = models["sphere"]
+    st = w.stations[:5]
+    alone, info = run_alone(w, h, st, 5e-3, 11)
+    assert info[0] % CHUNK == 0 and info[0] >= 2 * CHUNK
+    # the same request among others (other models, station counts, targets)
+    sv = server(w, streams=4)
+    try:
+        reqs = []
+        wv, hv = models["voxel"]
+        reqs.append((M.mcg_submit(sv, hv, wv.stations[:7], 2e-2, 3), 7))
+        reqs.append((M.mcg_submit(sv, h, w.stations[2:8], 1e-2, 5), 6))
+        target = M.mcg_submit(sv, h, st, 5e-3, 11)
+        reqs.append((M.mcg_submit(sv, hv, wv.stations[10:12], 1e-2, 9), 2))
+        rc, mixed = M.mcg_wait(target, 5, 120_000)
+        assert rc == M.MCG_OK
+        for rq, S in reqs:
+            assert M.mcg_wait(rq, S, 120_000)[0] == M.MCG_OK
+            M.mcg_request_free(rq)
+        M.mcg_request_free(target)
+    finally:
+        M.mcg_server_destroy(sv)
+    for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps"):
+        assert np.array_equal(alone[k], mixed[k]), k
+
+
+def test_server_equals_device_solve(models):
+    w, h = models["sphere"]
+    st = w.stations[:3]
+    out, (paths, rounds, _) = run_alone(w, h, st, 8e-3, 2)
+    ds = DeviceSolve(w.with_(seed=2), stations=st, batch=CHUNK, precision=M.MCG_MIXED)
+    ref = ds.run(paths=paths)
+    for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps"):
+        assert np.array_equal(out[k], ref[k]), k
+
+
+def test_stops_at_target_and_respects_cap(models):
+    w, h = models["sphere"]
+    out, (paths, rounds, _) = run_alone(w, h, w.stations[:4], 4e-3, 1)
+    assert np.all(out["se_u"] <= 4e-3 * np.abs(out["u"]))
+    # one round fewer would not have met the target at some station
+    ds = DeviceSolve(w.with_(seed=1), stations=w.stations[:4], batch=CHUNK, precision=M.MCG_MIXED)
+    prev = ds.run(paths=paths - CHUNK)
+    assert paths == 2 * CHUNK or np.any(prev["se_u"] > 4e-3 * np.abs(prev["u"]))
+    # max_paths caps an unreachable target
+    sv = server(w, max_paths=3 * CHUNK)
+    try:
+        rq = M.mcg_submit(sv, h, w.stations[:2], 1e-9, 1)
+        rc, out = M.mcg_wait(rq, 2, 120_000)
+        assert rc == M.MCG_OK and np.all(out["n_paths"] == 3 * CHUNK)
+        M.mcg_request_free(rq)
+    finally:
+        M.mcg_server_destroy(sv)
+
+
+def test_cancel_and_budget_queueing(models):
+    w, h = models["prism"]
+    sv = server(w, hbm_budget=1 << 20, streams=2)   # one request in flight at a time
+    try:
+        long_rq = M.mcg_submit(sv, h, w.stations[:2], 1e-7, 4)
+        small = [M.mcg_submit(sv, models["sphere"][1], models["sphere"][0].stations[:1], 2e-2, s) for s in range(3)]
+        time.sleep(0.5)
+        M.mcg_cancel(long_rq)
+        rc, out = M.mcg_wait(long_rq, 2, 300_000)
+        assert rc == M.MCG_ERR_CANCELLED
+        for rq in small:
+            assert M.mcg_wait(rq, 1, 300_000)[0] == M.MCG_OK
+            M.mcg_request_free(rq)
+        M.mcg_request_free(long_rq)
+    finally:
+        M.mcg_server_destroy(sv)
+
+
+def test_submit_validation(models):
+    w, h = models["sphere"]
+    sv = server(w)
+    try:
+        with pytest.raises(M.McgError):
+            M.mcg_submit(sv, h, np.array([[0.0, 0.0, 2.0]]), 1e-2, 0)
+        with pytest.raises(M.McgError):
+            M.mcg_submit(sv, h, w.stations[:1], -1.0, 0)
+    finally:
+        M.mcg_server_destroy(sv)
