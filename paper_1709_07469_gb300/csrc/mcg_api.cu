@@ -143,6 +143,25 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     P.lnscale_f = (float)(-2.0 * std::log(2.0) * P.sd * P.sd);
     P.crn = o->crn_gz ? 1 : 0;
     P.clip = o->clip ? 1 : 0;
+    // Conservative boxes for the walk's common step (all copies inside, no
+    // density at any copy): a margin of 1e-5 of the largest half-width
+    // covers the single-precision rounding of the tests several times over.
+    {
+        const double hmax = std::fmax(std::fmax(P.half_f[0], P.half_f[1]), P.half_f[2]);
+        const double margin = 1e-5 * hmax;
+        P.in_f[0] = (float)(P.half_f[0] - margin);
+        P.in_f[1] = (float)(P.half_f[1] - margin);
+        P.in_f[2] = (float)(P.half_f[2] - P.h - margin);
+        if (R->kind == MCG_RHO_PRISM) {
+            for (int k = 0; k < 3; ++k) {
+                P.far_c[k] = (float)(0.5 * ((double)P.plo_f[k] + (double)P.phi_f[k]));
+                P.far_h[k] = (float)(0.5 * ((double)P.phi_f[k] - (double)P.plo_f[k]) + margin + (k == 2 ? P.h : 0.0));
+            }
+        } else if (R->kind == MCG_RHO_SPHERE) {
+            const double rf = R->radius + P.h + margin;
+            P.far_r2 = (float)(rf * rf);
+        }
+    }
     P.max_steps = o->max_steps;
     P.key0 = (uint32_t)seed;
     P.key1 = (uint32_t)(seed >> 32);

@@ -16,6 +16,9 @@ struct WalkParams {
     // domain
     double lo[3], hi[3], cen[3];
     float half_f[3];
+    float in_f[3];                 // all three copies surely inside: |x_k| < in_f[k]
+    float far_c[3], far_h[3];      // density surely 0 at all copies outside this box
+    float far_r2;                  // ... or (sphere) beyond this squared radius
     // density
     int32_t rho_kind;
     double G, rho0;

@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // rho at the previous point
     unsigned alive = 0u;
     int64_t steps = 0;
+    bool zero_r = false;                  // r0..r2 are 0 (the last steps skipped the lookups)
     const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2];
     const float hf = CRN ? P.h_f : 0.0f;
     unsigned round = 0u;
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             alive = CRN ? 7u : 1u;
             blk = 0u;
             steps = 0;
+            zero_r = false;
             busy = true;
         }
         if (!__any_sync(kFull, busy)) break;
@@ -336,30 +338,55 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const float nx = wx + z[3 * m], ny = wy + z[3 * m + 1], nz = wz + z[3 * m + 2];
-                    const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
-                    unsigned ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
-                    if (CRN) {
-                        ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
-                        ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
+                    // common step: every copy surely inside Omega and surely
+                    // outside the density's support -> nothing to do but move
+                    const bool inside_all = fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] && fabsf(nz) < P.in_f[2];
+                    bool no_rho = true;
+                    if constexpr (RHO == MCG_RHO_PRISM) {
+                        no_rho = !(fabsf(nx - P.far_c[0]) <= P.far_h[0] && fabsf(ny - P.far_c[1]) <= P.far_h[1] &&
+                                   fabsf(nz - P.far_c[2]) <= P.far_h[2]);
+                    } else if constexpr (RHO == MCG_RHO_SPHERE) {
+                        const float dx = nx - P.sc_f[0], dy = ny - P.sc_f[1], dz = nz - P.sc_f[2];
+                        no_rho = dx * dx + dy * dy + dz * dz > P.far_r2;
+                    } else if constexpr (RHO == MCG_RHO_VOXEL) {
+                        no_rho = false;
                     }
-                    const unsigned out = alive & ~ins;
-                    if (out) {  // rare: some copy left Omega on this step
-                        const int64_t nstep = 4 * (int64_t)blk + m + 1;
-                        if (out & 1u) put_exit(P, 0, item, wx, wy, wz, nx, ny, nz, S0, r0, D0);
-                        if (CRN && (out & 2u)) put_exit(P, 1, item, wx, wy, wz + hf, nx, ny, nz + hf, S1, r1, D1);
-                        if (CRN && (out & 4u)) put_exit(P, 2, item, wx, wy, wz - hf, nx, ny, nz - hf, S2, r2, D2);
-                        steps += nstep * (int64_t)__popc(out);
-                        alive &= ins;
-                    }
-                    float ra, rb, rc;
-                    rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
-                    S0 += ra;
-                    r0 = ra;
-                    if (CRN) {
-                        S1 += rb;
-                        S2 += rc;
-                        r1 = rb;
-                        r2 = rc;
+                    if (inside_all && no_rho) {
+                        zero_r = true;  // rho = 0 at every copy: the partial sums do not change
+                    } else {
+                        if (zero_r) {
+                            r0 = r1 = r2 = 0.f;
+                            zero_r = false;
+                        }
+                        if (!inside_all) {
+                            const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
+                            unsigned ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
+                            if (CRN) {
+                                ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
+                                ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
+                            }
+                            const unsigned out = alive & ~ins;
+                            if (out) {  // some copy left Omega on this step
+                                const int64_t nstep = 4 * (int64_t)blk + m + 1;
+                                if (out & 1u) put_exit(P, 0, item, wx, wy, wz, nx, ny, nz, S0, r0, D0);
+                                if (CRN && (out & 2u))
+                                    put_exit(P, 1, item, wx, wy, wz + hf, nx, ny, nz + hf, S1, r1, D1);
+                                if (CRN && (out & 4u))
+                                    put_exit(P, 2, item, wx, wy, wz - hf, nx, ny, nz - hf, S2, r2, D2);
+                                steps += nstep * (int64_t)__popc(out);
+                                alive &= ins;
+                            }
+                        }
+                        float ra, rb, rc;
+                        rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
+                        S0 += ra;
+                        r0 = ra;
+                        if (CRN) {
+                            S1 += rb;
+                            S2 += rc;
+                            r1 = rb;
+                            r2 = rc;
+                        }
                     }
                     wx = nx;
                     wy = ny;
