@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--capped-only", action="store_true",
                     help="only the tail-free stepping-rate launches (small profiling case)")
+    ap.add_argument("--serving", action="store_true",
+                    help="replay a Poisson trace of solve requests over 16 voxel models through the server")
+    ap.add_argument("--requests", type=int, default=200, help="requests in the serving trace")
+    ap.add_argument("--rate", type=float, default=200.0, help="mean arrival rate of the serving trace (1/s)")
     return ap.parse_args()
 
 
@@ -316,7 +320,8 @@ def run_ours(args):
         if not args.skip_fp64:
             out["fp64_walk"] = fp64_comparison(M, w, dev)
         if not args.skip_e2e:
-            out["e2e"] = e2e_solve(M, w, Bp, max(1, min(args.steps, 3)))
+            out["e2e"] = e2e_server(M, w, Bp, args.steps)
+            out["e2e_blocking_solve"] = e2e_solve(M, w, Bp, max(1, min(args.steps, 3)))
         if not args.skip_cpu:
             rate, dt, cores, _ = cpu_oracle_rate(w, args.cpu_paths)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -386,9 +391,10 @@ def fp64_comparison(M, w, dev):
 
 
 def e2e_solve(M, w, Bp, steps):
-    """The public one-call API with HOST stations and HOST results: each step
-    is mcgrav_solve over the step's batch (workspace allocation, host->device
-    copy of the stations, walk, reduction, device->host copy of the results)."""
+    """The blocking one-call API with HOST stations and HOST results: each
+    step is mcgrav_solve over the step's batch (workspace allocation,
+    host->device copy of the stations, walk, reduction, device->host copy of
+    the results).  One stream: the exit-time tail of each call is exposed."""
     import torch
     prob = M.problem(w)
     opts = M.options(w, precision=M.MCG_MIXED, batch_paths=Bp)
@@ -405,14 +411,122 @@ def e2e_solve(M, w, Bp, steps):
         total_steps += float(r.path_steps.sum())
     S = w.n_stations
     return {"value": total_steps / t, "unit": UNIT, "h2d_bytes_per_step": S * 3 * 8,
+            "d2h_bytes_per_step": S * 6 * 8 + 4, "steps": steps, "api": "mcgrav_solve (blocking, one stream)"}
+
+
+def e2e_server(M, w, Bp, steps):
+    """The asynchronous public API end to end: each step is one request
+    (mcg_submit with HOST stations) of the 30 stations x Bp paths, walked in
+    one round whose station results are copied back to HOST memory; the step
+    ends when mcg_wait returns.  Requests run on their own streams, so each
+    request's exit-time tail runs beside the other requests' walks.
+    Wall-clock time from the first submit to the last completion."""
+    import torch
+    S = w.n_stations
+    model = M.mcg_model_create(M.problem(w), w.dt, w.h)
+    cfg = M.server_config(M.options(w, precision=M.MCG_MIXED), chunk_paths=Bp, min_paths=Bp, max_paths=Bp,
+                          streams=max(2, min(steps, 8)), max_active=max(8, steps), hbm_budget=32 << 30)
+    sv = M.mcg_server_create(cfg)
+    try:
+        warm = M.mcg_submit(sv, model, w.stations, 1e-12, 10**6)
+        M.mcg_wait(warm, S)
+        M.mcg_request_free(warm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reqs = [M.mcg_submit(sv, model, w.stations, 1e-12, 1000 + k) for k in range(steps)]
+        total_steps = 0.0
+        for rq in reqs:
+            rc, out = M.mcg_wait(rq, S)
+            assert rc == M.MCG_OK, M.last_error()
+            total_steps += float(out["path_steps"].sum())
+        t = time.perf_counter() - t0
+        for rq in reqs:
+            M.mcg_request_free(rq)
+    finally:
+        M.mcg_server_destroy(sv)
+        M.mcg_model_destroy(model)
+    return {"value": total_steps / t, "unit": UNIT, "h2d_bytes_per_step": S * 3 * 8,
             "d2h_bytes_per_step": S * 6 * 8 + 4, "steps": steps,
-            "api": "mcgrav_solve (blocking, host buffers, one stream: exit-time tail not overlapped)"}
+            "api": "mcg_submit / mcg_wait (server; one request per step, one stream per request)"}
+
+
+def run_serving(args):
+    """Serving mix: 16 device-resident voxel models (GRF density, boundary
+    tables), Poisson arrivals, 1-64 stations per request, relative-SE targets
+    drawn from {1e-2, 3e-3, 1e-3}; requests are submitted at their arrival
+    times and complete as the server's rounds meet their targets."""
+    import torch
+
+    from paper_1709_07469_gb300 import build as B
+    from paper_1709_07469_gb300 import mcgrav as M
+    from paper_1709_07469_gb300 import workloads as W
+    from paper_1709_07469_gb300.device import voxel_model
+
+    B.build()
+    M.load()
+    base = W.voxel_survey()
+    models = []
+    t0 = time.perf_counter()
+    for k in range(16):
+        wk = base.with_(grid_seed=k)
+        grid, faces = voxel_model(wk)
+        models.append(M.mcg_model_create(M.problem(wk, grid=grid, faces=faces), wk.dt, wk.h))
+        del grid, faces
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(1234)
+    n = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n))
+    S = rng.integers(1, 65, n)
+    targets = rng.choice([1e-2, 3e-3, 1e-3], n)
+    mk = rng.integers(0, 16, n)
+    st_idx = [rng.choice(base.n_stations, size=int(s), replace=False) for s in S]
+    cfg = M.server_config(M.options(base, precision=M.MCG_MIXED), chunk_paths=4096, min_paths=8192,
+                          hbm_budget=16 << 30, streams=8, max_active=64)
+    sv = M.mcg_server_create(cfg)
+    reqs = [None] * n
+    t_start = time.perf_counter()
+    i = 0
+    lat, path_steps, stations_done = [], 0, 0
+    outstanding = set()
+    while i < n or outstanding:
+        now = time.perf_counter() - t_start
+        while i < n and arrivals[i] <= now:
+            reqs[i] = M.mcg_submit(sv, models[mk[i]], base.stations[st_idx[i]], float(targets[i]), i)
+            outstanding.add(i)
+            i += 1
+        for j in list(outstanding):
+            done, rc, out = M.mcg_poll(reqs[j], int(S[j]))
+            if done:
+                assert rc == M.MCG_OK, (j, rc, M.last_error())
+                lat.append(M.mcg_request_info(reqs[j])[2] * 1e3)
+                path_steps += int(out["path_steps"].sum())
+                stations_done += int(S[j])
+                M.mcg_request_free(reqs[j])
+                outstanding.discard(j)
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t_start
+    M.mcg_server_destroy(sv)
+    for m in models:
+        M.mcg_model_destroy(m)
+    line = {"metric": "serving: p50/p99 ms and stations/s over a Poisson request trace", "impl": "ours",
+            "requests": n, "rate_per_s": args.rate, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "stations_per_s": stations_done / makespan,
+            "path_steps_per_s": path_steps / makespan, "makespan_s": makespan,
+            "offered_span_s": float(arrivals[-1]), "model_setup_s": setup_s,
+            "config": {"workload": "voxel_survey x 16 models (seeds 0-15)", "stations_per_request": "U{1..64}",
+                       "targets": [1e-2, 3e-3, 1e-3], "chunk_paths": 4096, "streams": 8, "hbm_budget_gib": 16},
+            "data": "synthetic", "dtype": "f32 step / f64 accumulate"}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
     if args.capped_only:
         import torch
         from paper_1709_07469_gb300 import build as B
