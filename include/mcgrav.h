@@ -126,6 +126,16 @@ typedef struct {
     int64_t batch_paths;     /* paths per station per launch in mcgrav_solve (0 = auto) */
     void* stream;            /* cudaStream_t (NULL = default stream)               */
     volatile int32_t* cancel;/* optional host-mapped flag; nonzero stops new work   */
+    int32_t bridge;          /* 1: Brownian-bridge exit test on steps that stay
+                                inside (the paper's Remark on exit times, after
+                                Gobet): a step from X to Y also ends the walk with
+                                probability 1 - prod_faces (1 - exp(-2 d_X d_Y /
+                                (sigma^2 dt))), one uniform per RNG-step from
+                                Philox counter (n/4, p, s, 2) word n%4 shared by
+                                the copies; the walk then ends on the face with the
+                                largest term, below Y, after a full step (default 0) */
+    int32_t refill_min;      /* a warp refills its lanes once at least this many are
+                                free (1..32, default 1; mcg_autotune picks it)    */
 } mcg_options;
 
 /* Per-station outputs (caller-owned, length S; any pointer may be NULL). */
@@ -248,6 +258,22 @@ MCG_API int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double*
  *   parts: HOST, R x S states (rank-major).  out: HOST, S states (may alias
  *   parts[0 .. S-1]).  States with n = 0 are skipped.  Allocates nothing. */
 MCG_API int mcg_states_merge(const mcg_station_state* parts, int64_t R, int64_t S, mcg_station_state* out);
+
+/* mcg_autotune: picks opts->block (64, 96, 128) and opts->refill_min (1, 4,
+ * 16) for this problem by timing short walks of the given stations (paths
+ * capped at 2048 RNG-steps so every lane stays busy) and writes the fastest
+ * pair into *opts.  stations_dev: DEVICE, S x 3.  Blocking; allocates and
+ * frees a scratch area of mcg_walk's size for S x 2048 paths. */
+MCG_API int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
+                         const double* stations_dev, int64_t S, double dt, uint64_t seed, mcg_options* opts);
+
+/* mcg_smooth_moving_average: the moving average the paper applies to the
+ * potential along a line of stations before differencing (Sec. 4.1, MATLAB
+ * smooth): out[i] = mean of y[i-k .. i+k] with k = min((span-1)/2, i,
+ * n-1-i), i.e. the window shrinks symmetrically at the ends (out[0] = y[0],
+ * out[n-1] = y[n-1]).  An even span is reduced by one.  HOST arrays; out may
+ * not alias y.  Allocates nothing. */
+MCG_API int mcg_smooth_moving_average(const double* y, int64_t n, int32_t span, double* out);
 
 /* Bytes of device workspace mcgrav_solve uses for S stations and batches of
  * `batch` paths per station. */

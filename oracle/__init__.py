@@ -68,7 +68,7 @@ class Problem(C.Structure):
         ("nu", C.c_int32), ("nv", C.c_int32), ("poly", C.c_double * 11),
         ("dt", C.c_double), ("sigma", C.c_double), ("h", C.c_double),
         ("seed", C.c_uint64), ("clip", C.c_int), ("crn", C.c_int), ("ubits", C.c_int),
-        ("max_steps", C.c_int64),
+        ("max_steps", C.c_int64), ("bridge", C.c_int),
     ]
 
 
@@ -137,6 +137,7 @@ class Spec:
     crn: int = 1
     ubits: int = 32
     max_steps: int = 1 << 40
+    bridge: int = 0
     _keep: list = field(default_factory=list, repr=False)
 
     def struct(self) -> Problem:
@@ -163,6 +164,7 @@ class Spec:
         p.dt, p.sigma, p.h = self.dt, self.sigma, self.h
         p.seed, p.clip, p.crn, p.ubits = self.seed, self.clip, self.crn, self.ubits
         p.max_steps = self.max_steps
+        p.bridge = self.bridge
         return p
 
 

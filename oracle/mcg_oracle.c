@@ -309,6 +309,34 @@ static int strictly_inside(const orc_problem* P, const double y[3])
     return 1;
 }
 
+/* Brownian-bridge exit test of one inside step X -> Y (the paper's Remark on
+ * exit-time estimation, after Gobet): for the plane of face k at distances
+ * d_X, d_Y the bridge crosses it with probability exp(-2 d_X d_Y / s^2),
+ * s = sigma sqrt(dt); the faces are treated as independent, so the step
+ * exits with probability 1 - prod_k (1 - p_k).  One uniform per RNG-step,
+ * Philox counter (n / 4, p, s, 2) word n % 4, shared by the CRN copies.
+ * Returns the face (2k lower, 2k+1 upper) with the largest p_k when the
+ * step exits, -1 otherwise. */
+static int bridge_exit(const orc_problem* P, const double X[3], const double Y[3], double sd,
+                       uint32_t s, uint32_t p, uint32_t n)
+{
+    double q = 1.0, pmax = -1.0;
+    int kmax = -1;
+    for (int f = 0; f < 6; ++f) {
+        int k = f / 2;
+        double dX = (f & 1) ? P->hi[k] - X[k] : X[k] - P->lo[k];
+        double dY = (f & 1) ? P->hi[k] - Y[k] : Y[k] - P->lo[k];
+        double pk = exp(-2.0 * dX * dY / (sd * sd));
+        q *= 1.0 - pk;
+        if (pk > pmax) { pmax = pk; kmax = f; }
+    }
+    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+    uint32_t ctr[4] = {n / 4u, p, s, 2u}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double U = uniform_open(w[n % 4u], P->ubits);
+    return (U < 1.0 - q) ? kmax : -1;
+}
+
 int orc_walk_path(const orc_problem* P, const double x0[3], uint32_t s, uint32_t p,
                   double u[3], int64_t steps[3], double xexit[9])
 {
@@ -345,11 +373,25 @@ int orc_walk_path(const orc_problem* P, const double x0[3], uint32_t s, uint32_t
             double Y[3] = {Wn[0], Wn[1], Wn[2] + off[c]};
             steps[c] += 1;
             if (strictly_inside(P, Y)) {
-                /* Step 3: trapezoid rule for the source integral. */
-                double r = orc_rho(P, Y);
+                int kb = -1;
+                if (P->bridge) kb = bridge_exit(P, X, Y, sd, s, p, (uint32_t)n);
+                if (kb < 0) {
+                    /* Step 3: trapezoid rule for the source integral. */
+                    double r = orc_rho(P, Y);
+                    I[c] += 0.5 * (rho_prev[c] + r) * P->dt;
+                    rho_prev[c] = r;
+                    any = 1;
+                    continue;
+                }
+                /* The Brownian bridge between X and Y left Omega through face
+                 * kb: the walk ends on that face, below Y, after a full step. */
+                double xs[3] = {Y[0], Y[1], Y[2]};
+                xs[kb / 2] = (kb & 1) ? P->hi[kb / 2] : P->lo[kb / 2];
+                double r = orc_rho(P, xs);
                 I[c] += 0.5 * (rho_prev[c] + r) * P->dt;
-                rho_prev[c] = r;
-                any = 1;
+                u[c] = orc_g(P, xs) - two_pi_G * I[c];
+                xexit[3 * c] = xs[0]; xexit[3 * c + 1] = xs[1]; xexit[3 * c + 2] = xs[2];
+                alive[c] = 0;
                 continue;
             }
             /* Step 4: the walk has left Omega. */

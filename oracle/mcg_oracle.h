@@ -53,6 +53,7 @@ typedef struct {
     int    crn;                    /* 1: walk x0, x0+h ez, x0-h ez together */
     int    ubits;                  /* 32: u=(w+.5)2^-32 ; 23: u=((w>>9)+.5)2^-23 */
     int64_t max_steps;             /* cap on RNG-steps per path             */
+    int    bridge;                 /* 1: Brownian-bridge exit test on inside steps */
 } orc_problem;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Pinned against the

@@ -143,12 +143,20 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     P.lnscale_f = (float)(-2.0 * std::log(2.0) * P.sd * P.sd);
     P.crn = o->crn_gz ? 1 : 0;
     P.clip = o->clip ? 1 : 0;
+    P.bridge = o->bridge ? 1 : 0;
+    if (o->refill_min < 0 || o->refill_min > 32) return set_error(MCG_ERR_ARG, "refill_min must be in [0, 32]");
+    P.refill_min = o->refill_min > 0 ? o->refill_min : 1;
+    P.bridge_k = -2.0 / (P.sd * P.sd);
+    P.bridge_k_f = (float)P.bridge_k;
     // Conservative boxes for the walk's common step (all copies inside, no
     // density at any copy): a margin of 1e-5 of the largest half-width
     // covers the single-precision rounding of the tests several times over.
     {
         const double hmax = std::fmax(std::fmax(P.half_f[0], P.half_f[1]), P.half_f[2]);
-        const double margin = 1e-5 * hmax;
+        // with the bridge test, steps within 6 sd of a face take the exact
+        // path: beyond that exp(-2 d_X d_Y / sd^2) < exp(-72) is below any
+        // uniform the generator can produce
+        const double margin = 1e-5 * hmax + (P.bridge ? 6.0 * P.sd : 0.0);
         P.in_f[0] = (float)(P.half_f[0] - margin);
         P.in_f[1] = (float)(P.half_f[1] - margin);
         P.in_f[2] = (float)(P.half_f[2] - P.h - margin);
@@ -260,6 +268,8 @@ void mcg_options_default(mcg_options* o)
     o->batch_paths = 0;
     o->stream = nullptr;
     o->cancel = nullptr;
+    o->bridge = 0;
+    o->refill_min = 1;
 }
 
 const char* mcg_last_error(void) { return g_err; }

@@ -39,7 +39,9 @@ struct WalkParams {
     // walk
     double dt, sd, h, two_pi_G;
     float sd_f, h_f, lnscale_f;    // lnscale_f = -2 ln 2 sd^2
-    int32_t crn, clip;
+    int32_t crn, clip, bridge, refill_min;
+    float bridge_k_f;              // -2 / (sigma^2 dt), single precision
+    double bridge_k;               // -2 / (sigma^2 dt)
     int64_t max_steps;
     uint32_t key0, key1;
     // work list: item i -> station i / N, path p0 + i % N

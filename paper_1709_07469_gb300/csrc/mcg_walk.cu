@@ -72,6 +72,8 @@ __device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsi
     return ok;
 }
 
+__device__ __forceinline__ int64_t nstep_of(uint32_t blk, int m) { return 4 * (int64_t)blk + m + 1; }
+
 __device__ __forceinline__ bool cancelled(const WalkParams& P)
 {
     int c = 0;
@@ -196,6 +198,82 @@ __device__ __forceinline__ void write_path(const WalkParams& P, unsigned long lo
 }
 
 // ---------------------------------------------------------------------------
+// Brownian-bridge exit test of an inside step X -> Y (the paper's Remark on
+// exit-time estimation, after Gobet): the bridge crosses the plane of a face
+// at distances d_X, d_Y with probability exp(-2 d_X d_Y / sd^2); with the
+// faces taken as independent the step exits with probability
+// 1 - prod (1 - p_face).  One uniform per RNG-step n: Philox counter
+// (n / 4, p, s, 2), word n % 4, shared by the copies.  Returns the face with
+// the largest p (2k lower, 2k+1 upper) if the step exits, else -1.
+// ---------------------------------------------------------------------------
+__device__ __noinline__ int bridge_face_f64(const WalkParams& P, const double* X, const double* Y, uint32_t s,
+                                            uint32_t p, uint32_t n)
+{
+    double q = 1.0, pmax = -1.0;
+    int kmax = -1;
+    for (int f = 0; f < 6; ++f) {
+        const int k = f >> 1;
+        const double dX = (f & 1) ? __dadd_rn(P.hi[k], -X[k]) : __dadd_rn(X[k], -P.lo[k]);
+        const double dY = (f & 1) ? __dadd_rn(P.hi[k], -Y[k]) : __dadd_rn(Y[k], -P.lo[k]);
+        const double pk = exp(__ddiv_rn(__dmul_rn(__dmul_rn(-2.0, dX), dY), __dmul_rn(P.sd, P.sd)));
+        q = __dmul_rn(q, __dadd_rn(1.0, -pk));
+        if (pk > pmax) {
+            pmax = pk;
+            kmax = f;
+        }
+    }
+    const uint4 w = philox4x32_10(make_uint4(n >> 2, p, s, 2u), P.key0, P.key1);
+    const uint32_t word = (n & 3u) == 0u ? w.x : (n & 3u) == 1u ? w.y : (n & 3u) == 2u ? w.z : w.w;
+    return (u01_f64(word) < 1.0 - q) ? kmax : -1;
+}
+
+// Single-precision bridge test of the copies `cand` for step m of block blk
+// (walk position (wx, wy, wz) -> (nx, ny, nz), box-centre coordinates, copy c
+// shifted by +h, -h in z).  Returns the mask of copies that exit and, 3 bits
+// per copy, their faces.
+__device__ __noinline__ unsigned bridge_exits_f32(const WalkParams& P, unsigned cand, float wx, float wy, float wz,
+                                                  float nx, float ny, float nz, float hf, uint32_t s, uint32_t p,
+                                                  uint32_t blk, int m, unsigned* faces)
+{
+    const uint4 w = philox4x32_10(make_uint4(blk, p, s, 2u), P.key0, P.key1);
+    const uint32_t word = m == 0 ? w.x : m == 1 ? w.y : m == 2 ? w.z : w.w;
+    const float U = u01_f32(word);
+    const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2], K = P.bridge_k_f;
+    const float pxy[4] = {__expf(K * (wx + hx) * (nx + hx)), __expf(K * (hx - wx) * (hx - nx)),
+                          __expf(K * (wy + hy) * (ny + hy)), __expf(K * (hy - wy) * (hy - ny))};
+    float qxy = 1.0f, pbest = -1.0f;
+    int fbest = -1;
+    for (int f = 0; f < 4; ++f) {
+        qxy *= 1.0f - pxy[f];
+        if (pxy[f] > pbest) {
+            pbest = pxy[f];
+            fbest = f;
+        }
+    }
+    unsigned out = 0u, fb = 0u;
+    for (int c = 0; c < 3; ++c) {
+        if (!(cand & (1u << c))) continue;
+        const float off = c == 0 ? 0.0f : (c == 1 ? hf : -hf);
+        const float zX = wz + off, zY = nz + off;
+        const float plo = __expf(K * (zX + hz) * (zY + hz)), phi = __expf(K * (hz - zX) * (hz - zY));
+        const float q = qxy * (1.0f - plo) * (1.0f - phi);
+        if (U < 1.0f - q) {
+            int f = fbest;
+            float pb = pbest;
+            if (plo > pb) {
+                pb = plo;
+                f = 4;
+            }
+            if (phi > pb) f = 5;
+            out |= 1u << c;
+            fb |= (unsigned)f << (3 * c);
+        }
+    }
+    *faces = fb;
+    return out;
+}
+
+// ---------------------------------------------------------------------------
 // Plain double-precision walk.
 // ---------------------------------------------------------------------------
 template <bool CRN>
@@ -251,10 +329,19 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
                 steps += 1;
                 const bool inside = Y[0] > P.lo[0] && Y[0] < P.hi[0] && Y[1] > P.lo[1] && Y[1] < P.hi[1] &&
                                     Y[2] > P.lo[2] && Y[2] < P.hi[2];
-                if (inside) {
+                const int kb = (inside && P.bridge) ? bridge_face_f64(P, X, Y, s, p, (uint32_t)n) : -1;
+                if (inside && kb < 0) {
                     const double r = rho_f64(P, Y);
                     I[c] = __dadd_rn(I[c], __dmul_rn(__dmul_rn(0.5, __dadd_rn(rp[c], r)), P.dt));
                     rp[c] = r;
+                } else if (inside) {
+                    // the bridge left Omega: end on face kb below Y after a full step
+                    double xs[3] = {Y[0], Y[1], Y[2]};
+                    xs[kb >> 1] = (kb & 1) ? P.hi[kb >> 1] : P.lo[kb >> 1];
+                    const double r = rho_f64(P, xs);
+                    const double Ic = __dadd_rn(I[c], __dmul_rn(__dmul_rn(0.5, __dadd_rn(rp[c], r)), P.dt));
+                    u[c] = __dadd_rn(boundary_value(P, kb, xs), -__dmul_rn(P.two_pi_G, Ic));
+                    alive &= ~(1u << c);
                 } else {
                     u[c] = exit_fp64(P, X, dW, Y, I[c], rp[c]);
                     alive &= ~(1u << c);
@@ -288,7 +375,7 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 // branch, so the slow double-precision unit sees one instruction per copy per
 // 64 steps).
 // ---------------------------------------------------------------------------
-template <int RHO, bool CRN>
+template <int RHO, bool CRN, bool BRIDGE>
 __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
 {
     bool busy = false, exhausted = false;
@@ -376,6 +463,26 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                                 steps += nstep * (int64_t)__popc(out);
                                 alive &= ins;
                             }
+                            if (BRIDGE && alive) {  // within the bridge band of a face
+                                unsigned faces = 0u;
+                                const unsigned bx = bridge_exits_f32(P, alive, wx, wy, wz, nx, ny, nz, hf, s, p, blk, m,
+                                                                     &faces);
+                                if (bx) {
+                                    const float yb[3] = {nx, ny, nz};
+                                    for (int c = 0; c < 3; ++c) {
+                                        if (!(bx & (1u << c))) continue;
+                                        const float off = c == 0 ? 0.0f : (c == 1 ? hf : -hf);
+                                        float y3[3] = {yb[0], yb[1], yb[2] + off};
+                                        const int f = (int)((faces >> (3 * c)) & 7u);
+                                        y3[f >> 1] = (f & 1) ? P.half_f[f >> 1] : -P.half_f[f >> 1];
+                                        if (c == 0) put_exit(P, 0, item, wx, wy, wz, y3[0], y3[1], y3[2], S0, r0, D0);
+                                        if (c == 1) put_exit(P, 1, item, wx, wy, wz + hf, y3[0], y3[1], y3[2], S1, r1, D1);
+                                        if (c == 2) put_exit(P, 2, item, wx, wy, wz - hf, y3[0], y3[1], y3[2], S2, r2, D2);
+                                    }
+                                    steps += nstep_of(blk, m) * (int64_t)__popc(bx);
+                                    alive &= ~bx;
+                                }
+                            }
                         }
                         float ra, rb, rc;
                         rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
@@ -404,7 +511,8 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     busy = false;
                 }
             }
-            if (__any_sync(kFull, !busy && !exhausted)) break;  // a lane wants new work
+            // enough lanes want new work: leave the block loop to refill them
+            if (__popc(__ballot_sync(kFull, !busy && !exhausted)) >= P.refill_min) break;
         }
         // warp-uniform flush of the partial sums (at most 16 blocks = 64 steps each)
         D0 += (double)S0;
@@ -443,10 +551,10 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
     }
 }
 
-template <int RHO, bool CRN>
+template <int RHO, bool CRN, bool BRIDGE>
 cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t st)
 {
-    walk_mixed_kernel<RHO, CRN><<<grid, block, 0, st>>>(P);
+    walk_mixed_kernel<RHO, CRN, BRIDGE><<<grid, block, 0, st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -459,9 +567,18 @@ cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t 
 }
 
 template <int RHO>
+cudaError_t launch_mixed_rho(const WalkParams& P, int block, int grid, cudaStream_t st)
+{
+    if (P.crn) return P.bridge ? launch_mixed<RHO, true, true>(P, block, grid, st)
+                               : launch_mixed<RHO, true, false>(P, block, grid, st);
+    return P.bridge ? launch_mixed<RHO, false, true>(P, block, grid, st)
+                    : launch_mixed<RHO, false, false>(P, block, grid, st);
+}
+
+template <int RHO>
 const void* mixed_fn(bool crn)
 {
-    return crn ? (const void*)walk_mixed_kernel<RHO, true> : (const void*)walk_mixed_kernel<RHO, false>;
+    return crn ? (const void*)walk_mixed_kernel<RHO, true, false> : (const void*)walk_mixed_kernel<RHO, false, false>;
 }
 
 const void* kernel_fn(int precision, int rho_kind, bool crn)
@@ -502,18 +619,10 @@ cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStrea
         return cudaGetLastError();
     }
     switch (P.rho_kind) {
-    case MCG_RHO_SPHERE:
-        return crn ? launch_mixed<MCG_RHO_SPHERE, true>(P, block, (int)grid, st)
-                   : launch_mixed<MCG_RHO_SPHERE, false>(P, block, (int)grid, st);
-    case MCG_RHO_PRISM:
-        return crn ? launch_mixed<MCG_RHO_PRISM, true>(P, block, (int)grid, st)
-                   : launch_mixed<MCG_RHO_PRISM, false>(P, block, (int)grid, st);
-    case MCG_RHO_VOXEL:
-        return crn ? launch_mixed<MCG_RHO_VOXEL, true>(P, block, (int)grid, st)
-                   : launch_mixed<MCG_RHO_VOXEL, false>(P, block, (int)grid, st);
-    default:
-        return crn ? launch_mixed<MCG_RHO_NONE, true>(P, block, (int)grid, st)
-                   : launch_mixed<MCG_RHO_NONE, false>(P, block, (int)grid, st);
+    case MCG_RHO_SPHERE: return launch_mixed_rho<MCG_RHO_SPHERE>(P, block, (int)grid, st);
+    case MCG_RHO_PRISM: return launch_mixed_rho<MCG_RHO_PRISM>(P, block, (int)grid, st);
+    case MCG_RHO_VOXEL: return launch_mixed_rho<MCG_RHO_VOXEL>(P, block, (int)grid, st);
+    default: return launch_mixed_rho<MCG_RHO_NONE>(P, block, (int)grid, st);
     }
 }
 

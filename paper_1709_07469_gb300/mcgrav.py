@@ -45,7 +45,8 @@ class mcg_boundary(C.Structure):
 class mcg_options(C.Structure):
     _fields_ = [("h", C.c_double), ("sigma", C.c_double), ("precision", C.c_int32), ("clip", C.c_int32),
                 ("crn_gz", C.c_int32), ("block", C.c_int32), ("max_steps", C.c_int64),
-                ("batch_paths", C.c_int64), ("stream", C.c_void_p), ("cancel", C.c_void_p)]
+                ("batch_paths", C.c_int64), ("stream", C.c_void_p), ("cancel", C.c_void_p),
+                ("bridge", C.c_int32), ("refill_min", C.c_int32)]
 
 
 class mcg_result(C.Structure):
@@ -108,6 +109,10 @@ def load(path: str | None = None):
     lib.mcg_walk_static.restype = C.c_int
     lib.mcg_walk_static_max_items.argtypes = []
     lib.mcg_walk_static_max_items.restype = C.c_int64
+    lib.mcg_autotune.argtypes = [P(mcg_domain), P(mcg_density), P(mcg_boundary), vp, i64, d, u64, P(mcg_options)]
+    lib.mcg_autotune.restype = C.c_int
+    lib.mcg_smooth_moving_average.argtypes = [vp, i64, i32, vp]
+    lib.mcg_smooth_moving_average.restype = C.c_int
     lib.mcg_states_merge.argtypes = [vp, i64, i64, vp]
     lib.mcg_states_merge.restype = C.c_int
     lib.mcg_server_config_default.argtypes = [P(mcg_server_config)]
@@ -228,7 +233,7 @@ def options(w=None, precision: int = MCG_MIXED, stream=None, **kw) -> mcg_option
     load().mcg_options_default(C.byref(o))
     o.precision = precision
     if w is not None:
-        o.h, o.sigma, o.clip, o.crn_gz = w.h, w.sigma, w.clip, w.crn
+        o.h, o.sigma, o.clip, o.crn_gz, o.bridge = w.h, w.sigma, w.clip, w.crn, w.bridge
     o.stream = _stream_handle(stream)
     for k, v in kw.items():
         setattr(o, k, v)
@@ -418,3 +423,17 @@ def mcg_request_info(request: int):
 
 def mcg_request_free(request: int) -> int:
     return _check(load().mcg_request_free(request))
+
+
+def mcg_autotune(prob: Problem, stations_dev, S: int, dt: float, seed: int, opts: mcg_options) -> mcg_options:
+    """Picks block and refill_min in place (returns opts)."""
+    _check(load().mcg_autotune(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary),
+                               _ptr(stations_dev), S, dt, seed & 0xFFFFFFFFFFFFFFFF, C.byref(opts)))
+    return opts
+
+
+def mcg_smooth_moving_average(y, span: int = 5) -> np.ndarray:
+    a = np.ascontiguousarray(y, dtype=np.float64)
+    out = np.empty_like(a)
+    _check(load().mcg_smooth_moving_average(a.ctypes.data, a.size, span, out.ctypes.data))
+    return out

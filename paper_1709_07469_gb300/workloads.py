@@ -55,6 +55,7 @@ class Workload:
     poly: tuple = (0.0,) * 11
     clip: int = 1
     crn: int = 1
+    bridge: int = 0
 
     @property
     def n_stations(self) -> int:
@@ -109,6 +110,17 @@ def voxel_survey(paths: int = 1_000_000, seed: int = 0, step: float = 10.0, grid
                     dt=step * step, h=1.0, seed=seed, paths=paths,
                     grid_shape=(nx, ny, nz), grid_origin=(-2000.0, -2000.0, -2000.0),
                     grid_spacing=spacing, grid_seed=grid_seed, table_n=table_n)
+
+
+def large_survey(paths: int = 1_000_000, seed: int = 0, step: float = 10.0, grid_seed: int = 0,
+                 shape=(128, 128, 64), table_n=(256, 256)) -> Workload:
+    """The voxel model of voxel_survey with 2 x 10^4 stations: a 100 x 100
+    surface grid at 20 m spacing (x, y = -990 + 20 i) at z = 0 and the same
+    grid airborne at z = +100 m."""
+    base = voxel_survey(paths=paths, seed=seed, step=step, grid_seed=grid_seed, shape=shape, table_n=table_n)
+    c = -990.0 + 20.0 * np.arange(100)
+    pts = [(x, y, z) for z in (0.0, 100.0) for y in c for x in c]
+    return base.with_(name="large_survey", stations=np.array(pts))
 
 
 def unit_box(stations, rho_kind="none", g_kind="poly", poly=(0.0,) * 11, dt=1e-2, paths=4000,

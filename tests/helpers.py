@@ -21,7 +21,7 @@ def oracle_spec(w: Workload, grid=None, faces=None, ubits: int = 32, max_steps: 
         radius=w.radius, plo=w.plo, phi=w.phi, grid=grid, origin=w.grid_origin,
         spacing=w.grid_spacing, g_kind=_G[w.g_kind], faces=faces, poly=w.poly, dt=w.dt,
         sigma=w.sigma, h=w.h, seed=w.seed, clip=w.clip, crn=w.crn, ubits=ubits,
-        max_steps=max_steps)
+        max_steps=max_steps, bridge=w.bridge)
 
 
 def smooth_tables(w: Workload, seed: int = 1, scale: float = 1e-4) -> np.ndarray:

@@ -131,3 +131,38 @@ def test_voxel_walk_mixed_paired(voxel_inputs):
         se = diff.std(ddof=1) / math.sqrt(diff.size)
         um = abs(ref.pp_u[s].mean())
         assert abs(diff.mean()) <= 4 * se + 1e-6 * um, (s, diff.mean(), se)
+
+
+def test_large_survey_full_size_sampled_paths(voxel_inputs):
+    """The 2 x 10^4-station survey in one launch (8 paths per station, mixed
+    precision); sampled (station, path) pairs are walked one by one by the
+    oracle under the same station and path indices (same random streams, the
+    23-bit uniforms of the single-precision walk)."""
+    _, grid, faces = voxel_inputs
+    w = W.large_survey(paths=8)
+    ds = DeviceSolve(w, batch=8, precision=M.MCG_MIXED, grid=torch.from_numpy(grid).cuda(),
+                     faces=torch.from_numpy(faces).cuda())
+    ds.reset()
+    ds.walk(0)
+    u, d, steps = ds.per_path()
+    assert int(ds.status[0].item()) == 0 and u.shape == (20000, 8)
+    spec = oracle_spec(w, grid=grid, faces=faces, ubits=23)
+    same, rel = [], []
+    for s in (0, 9999, 10000, 19999, 4321, 15678):
+        for p in range(8):
+            rc, uc, st, _ = oracle.walk_path(spec, w.stations[s], s, p)
+            assert rc == 0
+            same.append(st.sum() == steps[s, p])
+            if same[-1]:
+                rel.append(abs(u[s, p] - uc[0]) / abs(uc[0]))
+    assert np.mean(same) > 0.8
+    assert np.median(rel) < 1e-5
+
+
+def test_autotune_picks_a_valid_launch_shape():
+    w = W.sphere_line()
+    ds = DeviceSolve(w, precision=M.MCG_MIXED)
+    M.mcg_autotune(ds.prob, ds.stations, ds.S, w.dt, w.seed, ds.opts)
+    assert ds.opts.block in (64, 96, 128) and ds.opts.refill_min in (1, 4, 16)
+    r = ds.run()
+    assert r["status"] == 0

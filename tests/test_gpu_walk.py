@@ -221,3 +221,43 @@ def test_device_station_outside_flags_status():
     u, d, s, status = *ds.per_path(), int(ds.status[0].item())
     assert status & (1 << M.MCG_ERR_ARG)
     assert np.all(np.isnan(u[3])) and np.all(np.isfinite(u[[0, 1, 2, 4, 5, 6, 7]]))
+
+
+# --- Brownian-bridge exit test ------------------------------------------------
+
+def test_bridge_fp64_per_path():
+    """Stations near faces (where the bridge acts) and the sphere line, FP64
+    walk per path against the oracle with the bridge on."""
+    st = np.array([[0.95, 0.2, 0.0], [0.1, -0.93, 0.4], [0.0, 0.0, 0.0]])
+    w = W.unit_box(st, g_kind="poly", poly=HARMONIC[1], dt=2e-3, paths=2000, clip=1, h=0.02).with_(bridge=1)
+    flips, _ = compare_fp64(w, w.paths)
+    assert flips < 1e-3
+    w = W.sphere_line(paths=2000).with_(bridge=1)
+    flips, _ = compare_fp64(w, w.paths)
+    assert flips < 1e-3
+
+
+def test_bridge_mixed_paired():
+    w = W.sphere_line(paths=20000).with_(bridge=1)
+    u, d, st, status = gpu_per_path(w, M.MCG_MIXED)
+    assert status == 0
+    ref = oracle.solve(oracle_spec(w, ubits=23), w.stations, w.paths, per_path=True)
+    assert (st == ref.pp_steps).mean() > 0.95
+    for s in range(w.n_stations):
+        diff = u[s] - ref.pp_u[s]
+        se = diff.std(ddof=1) / math.sqrt(diff.size)
+        assert abs(diff.mean()) <= 4 * se + 1e-6 * abs(ref.pp_u[s].mean()), (s, diff.mean(), se)
+
+
+@pytest.mark.parametrize("precision", [M.MCG_FP64, M.MCG_MIXED])
+def test_bridge_slab_exit_time_gpu(precision):
+    """E[N dt] of the slab equals (a - z)(a + z) without overshoot correction."""
+    a = 0.5
+    st = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.3]])
+    w = W.Workload(name="slab", lo=(-20.0, -20.0, -a), hi=(20.0, 20.0, a), rho_kind="prism", g_kind="zero",
+                   G=1.0, stations=st, dt=1e-3, h=0.01, seed=5, paths=200_000 if precision else 50_000,
+                   rho0=1.0, plo=(-100.0,) * 3, phi=(100.0,) * 3, clip=0, crn=0, bridge=1)
+    r = DeviceSolve(w, precision=precision).run()
+    for s, z in enumerate(st[:, 2]):
+        got, se = -r["u"][s] / (2 * math.pi), r["se_u"][s] / (2 * math.pi)
+        assert abs(got - (a - z) * (a + z)) < 4 * se + 2e-4, (z, got, se)
