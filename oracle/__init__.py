@@ -59,6 +59,7 @@ def build(force: bool = False) -> str:
 class Problem(C.Structure):
     _fields_ = [
         ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("domain_kind", C.c_int), ("bc", C.c_double * 3), ("R", C.c_double),
         ("rho_kind", C.c_int), ("G", C.c_double), ("rho0", C.c_double),
         ("center", C.c_double * 3), ("radius", C.c_double),
         ("plo", C.c_double * 3), ("phi", C.c_double * 3),
@@ -116,6 +117,9 @@ class Spec:
     """Problem description in plain Python (mirrors the oracle's struct)."""
     lo: tuple
     hi: tuple
+    domain_kind: int = 0                  # 0 box, 1 ball |x - bc| < R
+    bc: tuple = (0.0, 0.0, 0.0)
+    R: float = 0.0
     rho_kind: int = RHO_NONE
     G: float = 1.0
     rho0: float = 0.0
@@ -143,6 +147,7 @@ class Spec:
     def struct(self) -> Problem:
         p = Problem()
         p.lo, p.hi = _v3(self.lo), _v3(self.hi)
+        p.domain_kind, p.bc, p.R = self.domain_kind, _v3(self.bc), self.R
         p.rho_kind, p.G, p.rho0 = self.rho_kind, self.G, self.rho0
         p.center, p.radius = _v3(self.center), self.radius
         p.plo, p.phi = _v3(self.plo), _v3(self.phi)

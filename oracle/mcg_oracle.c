@@ -304,9 +304,32 @@ double orc_g(const orc_problem* P, const double x[3])
 
 static int strictly_inside(const orc_problem* P, const double y[3])
 {
+    if (P->domain_kind == ORC_DOMAIN_BALL) {
+        double dx = y[0] - P->bc[0], dy = y[1] - P->bc[1], dz = y[2] - P->bc[2];
+        return dx * dx + dy * dy + dz * dz < P->R * P->R;
+    }
     for (int k = 0; k < 3; ++k)
         if (!(y[k] > P->lo[k] && y[k] < P->hi[k])) return 0;
     return 1;
+}
+
+/* Fraction theta in [0, 1] of the step X -> X + dW at which the segment
+ * leaves the ball |x - bc| < R: the positive root of
+ * |X - bc + theta dW|^2 = R^2, in the form without cancellation. */
+static double ball_theta(const orc_problem* P, const double X[3], const double dW[3])
+{
+    double a = 0.0, b = 0.0, c = -P->R * P->R;
+    for (int k = 0; k < 3; ++k) {
+        double q = X[k] - P->bc[k];
+        a += dW[k] * dW[k];
+        b += 2.0 * q * dW[k];
+        c += q * q;
+    }
+    double D = b * b - 4.0 * a * c;
+    double t = (b >= 0.0) ? (-2.0 * c) / (b + sqrt(D)) : (-b + sqrt(D)) / (2.0 * a);
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return t;
 }
 
 /* Brownian-bridge exit test of one inside step X -> Y (the paper's Remark on
@@ -397,7 +420,11 @@ int orc_walk_path(const orc_problem* P, const double x0[3], uint32_t s, uint32_t
             /* Step 4: the walk has left Omega. */
             double xs[3];
             double theta = 1.0;
-            if (P->clip) {
+            if (P->clip && P->domain_kind == ORC_DOMAIN_BALL) {
+                /* Clip the last segment where it leaves the ball. */
+                theta = ball_theta(P, X, dW);
+                for (int k = 0; k < 3; ++k) xs[k] = X[k] + theta * dW[k];
+            } else if (P->clip) {
                 /* Clip the last segment at the first face it crosses. */
                 int kstar = -1;
                 double tmin = INFINITY, bstar = 0.0;

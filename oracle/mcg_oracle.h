@@ -33,8 +33,12 @@ enum { ORC_RHO_NONE = 0, ORC_RHO_SPHERE = 1, ORC_RHO_PRISM = 2, ORC_RHO_VOXEL = 
 enum { ORC_G_ZERO = 0, ORC_G_SPHERE = 1, ORC_G_PRISM = 2, ORC_G_TABLE = 3, ORC_G_POLY = 4 };
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_STEP_CAP = 4 };
 
+enum { ORC_DOMAIN_BOX = 0, ORC_DOMAIN_BALL = 1 };
+
 typedef struct {
     double lo[3], hi[3];           /* box domain Omega = (lo, hi) open      */
+    int    domain_kind;            /* box, or the ball |x - bc| < R         */
+    double bc[3], R;
     int    rho_kind;
     double G;                      /* gravitational constant                */
     double rho0;                   /* sphere / prism density                */

@@ -56,6 +56,9 @@ class Workload:
     clip: int = 1
     crn: int = 1
     bridge: int = 0
+    domain: str = "box"                 # "box" (lo, hi) or "ball" (ball_center, ball_radius)
+    ball_center: tuple = (0.0, 0.0, 0.0)
+    ball_radius: float = 0.0
 
     @property
     def n_stations(self) -> int:
@@ -121,6 +124,24 @@ def large_survey(paths: int = 1_000_000, seed: int = 0, step: float = 10.0, grid
     c = -990.0 + 20.0 * np.arange(100)
     pts = [(x, y, z) for z in (0.0, 100.0) for y in c for x in c]
     return base.with_(name="large_survey", stations=np.array(pts))
+
+
+def paper_cube_ball(paths: int = 4096, seed: int = 0, step: float = 20.0, line: str = "horizontal",
+                    R: float = 10_000.0) -> Workload:
+    """The paper's own experiment (Sec. 3): a cube [0,100]^3 m of density
+    2000 kg/m^3 inside a ball of radius 10 km with zero Dirichlet data.
+    Experiment 1: stations on y = 50, z = 200, x = -100 .. 200 step 10 (31
+    points); experiment 2: the vertical line x = y = 50, z = -100 .. 200 step
+    10.  The paper's time step is given without units; here the step length
+    sigma sqrt(dt) is stated in metres."""
+    t = -100.0 + 10.0 * np.arange(31)
+    if line == "horizontal":
+        pts = np.stack([t, np.full(31, 50.0), np.full(31, 200.0)], axis=1)
+    else:
+        pts = np.stack([np.full(31, 50.0), np.full(31, 50.0), t], axis=1)
+    return Workload(name="paper_cube_ball", lo=(-R, -R, -R), hi=(R, R, R), rho_kind="prism", g_kind="zero",
+                    G=G_SI, stations=pts, dt=step * step, h=1.0, seed=seed, paths=paths, rho0=2000.0,
+                    plo=(0.0, 0.0, 0.0), phi=(100.0, 100.0, 100.0), domain="ball", ball_radius=R)
 
 
 def unit_box(stations, rho_kind="none", g_kind="poly", poly=(0.0,) * 11, dt=1e-2, paths=4000,

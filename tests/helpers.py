@@ -17,7 +17,8 @@ _G = {"zero": oracle.G_ZERO, "sphere": oracle.G_SPHERE, "prism": oracle.G_PRISM,
 
 def oracle_spec(w: Workload, grid=None, faces=None, ubits: int = 32, max_steps: int = 1 << 40) -> oracle.Spec:
     return oracle.Spec(
-        lo=w.lo, hi=w.hi, rho_kind=_RHO[w.rho_kind], G=w.G, rho0=w.rho0, center=w.center,
+        lo=w.lo, hi=w.hi, domain_kind=1 if w.domain == "ball" else 0, bc=w.ball_center, R=w.ball_radius,
+        rho_kind=_RHO[w.rho_kind], G=w.G, rho0=w.rho0, center=w.center,
         radius=w.radius, plo=w.plo, phi=w.phi, grid=grid, origin=w.grid_origin,
         spacing=w.grid_spacing, g_kind=_G[w.g_kind], faces=faces, poly=w.poly, dt=w.dt,
         sigma=w.sigma, h=w.h, seed=w.seed, clip=w.clip, crn=w.crn, ubits=ubits,

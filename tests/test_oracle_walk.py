@@ -267,3 +267,57 @@ def test_station_on_boundary_rejected():
 def test_step_cap_reported():
     w = W.unit_box([[0.0, 0.0, 0.0]], g_kind="poly", poly=HARMONIC["linear"], dt=1e-4)
     assert oracle.solve(oracle_spec(w, max_steps=5), w.stations, 10).status == oracle.ERR_STEP_CAP
+
+
+# --- ball domain (the paper's own Omega, Sec. 2.2 and Sec. 3) ----------------
+
+def _ball(stations, **kw):
+    base = dict(name="ball", lo=(-1.0,) * 3, hi=(1.0,) * 3, G=1.0, stations=np.asarray(stations), h=0.02, seed=3,
+                domain="ball", ball_radius=1.0)
+    base.update(kw)
+    return W.Workload(**base)
+
+
+def test_ball_constant_density_quadratic_unbiased():
+    """Delta Phi = 4 pi G rho0 in the ball with Phi = A (|x|^2 - R^2) on and
+    outside the boundary (A = 2 pi G rho0 / 3): exactly unbiased without
+    clipping, for u and for the centred difference."""
+    A = 2 * math.pi / 3
+    st = np.array([[0.0, 0.0, 0.3], [0.2, 0.1, -0.4], [0.5, 0.0, 0.0]])
+    w = _ball(st, rho_kind="prism", g_kind="poly", dt=4e-3, paths=20000, rho0=1.0, plo=(-5.0,) * 3,
+              phi=(5.0,) * 3, poly=(-A, 0, 0, 0, A, A, A, 0, 0, 0, 0), clip=0)
+    r = oracle.solve(oracle_spec(w), st, w.paths, threads=4)
+    for s, x in enumerate(st):
+        assert abs(r.u[s] - A * (x @ x - 1.0)) < 4 * r.se_u[s]
+        assert abs(r.gz[s] - 2 * A * x[2]) < 4 * r.se_gz[s]
+
+
+def test_ball_zero_dirichlet_offset_is_GM_over_R():
+    """The paper's boundary-error estimate (Sec. 2.2): zero Dirichlet data on
+    a ball of radius R around a compact mass M gives the Newtonian potential
+    plus the harmonic function equal to -Phi on the sphere, i.e. + G M / R
+    (constant; the cube's Phi on the sphere is -G M / R to O((a/R)^4)).
+    g_z is unaffected (the derivative of a constant is zero)."""
+    a = 0.05
+    M_ = (2 * a) ** 3
+    st = np.array([[0.0, 0.0, 0.3], [0.25, 0.0, -0.2], [0.0, 0.0, 0.6]])
+    w = _ball(st, rho_kind="prism", g_kind="zero", dt=1e-4, paths=20000, rho0=1.0, plo=(-a,) * 3, phi=(a,) * 3,
+              h=0.01, seed=4)
+    r = oracle.solve(oracle_spec(w), st, w.paths, threads=8)
+    for s, x in enumerate(st):
+        phi = oracle.prism_phi(1.0, 1.0, (-a,) * 3, (a,) * 3, x)
+        gz = oracle.prism_gz(1.0, 1.0, (-a,) * 3, (a,) * 3, x)
+        assert abs(r.u[s] - (phi + M_)) < 4 * r.se_u[s] + 2e-5
+        assert r.u[s] - phi > 10 * r.se_u[s]          # the offset is there
+        assert abs(r.gz[s] - gz) < 4 * r.se_gz[s]
+
+
+def test_ball_exit_points_on_the_sphere():
+    st = np.array([[0.0, 0.0, 0.9], [0.5, 0.5, 0.5]])
+    w = _ball(st, rho_kind="none", g_kind="poly", poly=HARMONIC["linear"], dt=0.01, paths=50, clip=1)
+    spec = oracle_spec(w)
+    for s, x in enumerate(st):
+        for p in range(50):
+            rc, u, steps, xe = oracle.walk_path(spec, x, s, p)
+            assert rc == 0
+            assert np.allclose(np.linalg.norm(xe, axis=1), 1.0, rtol=1e-12, atol=1e-12)
