@@ -428,7 +428,8 @@ def e2e_server(M, w, Bp, steps):
     S = w.n_stations
     model = M.mcg_model_create(M.problem(w), w.dt, w.h)
     cfg = M.server_config(M.options(w, precision=M.MCG_MIXED), chunk_paths=Bp, min_paths=Bp, max_paths=Bp,
-                          streams=max(2, min(steps, 8)), max_active=max(8, steps), hbm_budget=32 << 30)
+                          max_round_paths=Bp, streams=max(2, min(steps, 8)), max_active=max(8, steps),
+                          hbm_budget=32 << 30)
     sv = M.mcg_server_create(cfg)
     try:
         warm = M.mcg_submit(sv, model, w.stations, 1e-12, 10**6)

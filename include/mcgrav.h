@@ -65,9 +65,19 @@ typedef enum {
     MCG_ERR_CANCELLED = 7   /* cancelled through the cancel flag              */
 } mcg_status;
 
-/* Box domain Omega = (lo, hi) (open).  Stations, and for g_z the two shifted
- * copies x0 +- h e_z, must lie strictly inside. */
-typedef struct { double lo[3], hi[3]; } mcg_domain;
+typedef enum { MCG_DOMAIN_BOX = 0, MCG_DOMAIN_BALL = 1 } mcg_domain_kind;
+
+/* Domain Omega (open): the box (lo, hi), or the ball |x - center| < radius
+ * (the paper's own domain, Sec. 2.2 and Sec. 3: a large ball around the
+ * body with zero Dirichlet data).  Stations, and for g_z the two shifted
+ * copies x0 +- h e_z, must lie strictly inside.  Tabulated boundary data and
+ * the Brownian-bridge test need the box. */
+typedef struct {
+    double lo[3], hi[3];
+    int32_t kind;
+    double center[3];
+    double radius;
+} mcg_domain;
 
 typedef enum { MCG_RHO_NONE = 0, MCG_RHO_SPHERE = 1, MCG_RHO_PRISM = 2, MCG_RHO_VOXEL = 3 } mcg_rho_kind;
 
@@ -125,7 +135,9 @@ typedef struct {
     int64_t max_steps;       /* RNG-step cap per path (default 2^31)               */
     int64_t batch_paths;     /* paths per station per launch in mcgrav_solve (0 = auto) */
     void* stream;            /* cudaStream_t (NULL = default stream)               */
-    volatile int32_t* cancel;/* optional host-mapped flag; nonzero stops new work   */
+    volatile int32_t* cancel;/* optional DEVICE int32; nonzero stops new work (the
+                                walk polls it with a system-scope load; write it
+                                with an asynchronous copy on another stream)       */
     int32_t bridge;          /* 1: Brownian-bridge exit test on steps that stay
                                 inside (the paper's Remark on exit times, after
                                 Gobet): a step from X to Y also ends the walk with
@@ -306,7 +318,9 @@ MCG_API int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int6
  * (k+1)*chunk - 1 of each station for round k) and merges them into the
  * request's station statistics; after each round the request stops once
  * every station reaches its relative standard error target (and has at
- * least min_paths paths) or max_paths.  Rounds of different requests run on
+ * least min_paths paths) or max_paths.  Past min_paths a round walks as many
+ * chunks (up to max_round_paths) as the request's own per-path spread says
+ * it still needs, in one launch.  Rounds of different requests run on
  * a pool of streams and overlap on the GPU; a request's result depends only
  * on its own (seed, stations, target), never on what else is in flight.
  * All calls are thread-safe.  Objects are owned by the library until the
@@ -322,6 +336,9 @@ typedef struct {
     int64_t chunk_paths;      /* paths per station per round (default 4096)          */
     int64_t min_paths;        /* paths per station before the target is checked (default 2 chunks) */
     int64_t max_paths;        /* cap per station (default 10^7)                      */
+    int64_t max_round_paths;  /* paths per station in one round at most (default 16 chunks):
+                                 after min_paths the next round walks the chunks the
+                                 request's own spread says it still needs, in one launch */
     mcg_options walk;         /* walk options (precision, h, sigma, clip, crn_gz, block, max_steps) */
 } mcg_server_config;
 

@@ -100,6 +100,8 @@ def _lib_handle():
             lib.orc_grf_density.argtypes = [u64, i64, i64, i64, d, d, P(C.c_float), P(d)]
             lib.orc_table_nodes.argtypes = [P(Problem), P(i64), P(i64), P(i64), i64, C.c_int, P(d)]
             lib.orc_table_nodes.restype = C.c_int
+            lib.orc_voxel_field.argtypes = [P(Problem), P(d), i64, C.c_int, P(d), P(d)]
+            lib.orc_voxel_field.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -291,3 +293,17 @@ def table_nodes(spec: Spec, face, iu, iv, nu: int, nv: int, threads: int = 0) ->
     if rc != OK:
         raise ValueError(f"orc_table_nodes status {rc}")
     return out
+
+
+def voxel_field(spec: Spec, points, threads: int = 0, want_gz: bool = False):
+    """Phi (and dPhi/dz) of the voxel model at points [n,3] by direct prism sums."""
+    lib = _lib_handle()
+    st = spec.struct()
+    x = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    phi = np.empty(x.shape[0])
+    gz = np.empty(x.shape[0]) if want_gz else None
+    rc = lib.orc_voxel_field(C.byref(st), _ptr(x, C.c_double), x.shape[0], threads, _ptr(phi, C.c_double),
+                             _ptr(gz, C.c_double))
+    if rc != OK:
+        raise ValueError(f"orc_voxel_field status {rc}")
+    return (phi, gz) if want_gz else phi

@@ -651,3 +651,40 @@ int orc_table_nodes(const orc_problem* P, const int64_t* face, const int64_t* iu
     }
     return status;
 }
+
+int orc_voxel_field(const orc_problem* P, const double* x, int64_t n, int nthreads, double* phi, double* gz)
+{
+    if (P->rho_kind != ORC_RHO_VOXEL) return ORC_ERR_ARG;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t q = 0; q < n; ++q) {
+        double s = 0.0, c = 0.0, sg = 0.0, cg = 0.0;
+        for (int64_t z = 0; z < P->n[2]; ++z)
+            for (int64_t y = 0; y < P->n[1]; ++y)
+                for (int64_t xx = 0; xx < P->n[0]; ++xx) {
+                    double rho = P->grid[xx + P->n[0] * (y + P->n[1] * z)];
+                    if (rho == 0.0) continue;
+                    double lo[3] = {P->origin[0] + P->spacing[0] * (double)xx,
+                                    P->origin[1] + P->spacing[1] * (double)y,
+                                    P->origin[2] + P->spacing[2] * (double)z};
+                    double hi[3] = {lo[0] + P->spacing[0], lo[1] + P->spacing[1], lo[2] + P->spacing[2]};
+                    double v = orc_prism_phi(P->G, rho, lo, hi, x + 3 * q);
+                    double t = s + v;
+                    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+                    else c += (v - t) + s;
+                    s = t;
+                    if (gz) {
+                        double g = orc_prism_gz(P->G, rho, lo, hi, x + 3 * q);
+                        double tg = sg + g;
+                        if (fabs(sg) >= fabs(g)) cg += (sg - tg) + g;
+                        else cg += (g - tg) + sg;
+                        sg = tg;
+                    }
+                }
+        phi[q] = s + c;
+        if (gz) gz[q] = sg + cg;
+    }
+    return ORC_OK;
+}

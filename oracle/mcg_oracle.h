@@ -102,6 +102,10 @@ void orc_grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz,
                      double sigma_vox, double amp, float* grid_out, double* z_out);
 int  orc_table_nodes(const orc_problem* P, const int64_t* face, const int64_t* iu,
                      const int64_t* iv, int64_t n, int nthreads, double* out);
+/* Potential and dPhi/dz of the voxel model at arbitrary points (direct sum
+ * of the prism closed forms over all voxels). */
+int  orc_voxel_field(const orc_problem* P, const double* x, int64_t n, int nthreads,
+                     double* phi, double* gz);
 
 #ifdef __cplusplus
 }

@@ -45,13 +45,30 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
 {
     if (!D || !R || !B || !o) return set_error(MCG_ERR_ARG, "null domain/density/boundary/options");
     std::memset(&P, 0, sizeof(P));
-    if (!finite3(D->lo) || !finite3(D->hi)) return set_error(MCG_ERR_ARG, "domain bounds must be finite");
-    for (int k = 0; k < 3; ++k) {
-        if (!(D->lo[k] < D->hi[k])) return set_error(MCG_ERR_ARG, "domain lo[%d] >= hi[%d]", k, k);
-        P.lo[k] = D->lo[k];
-        P.hi[k] = D->hi[k];
-        P.cen[k] = 0.5 * (D->lo[k] + D->hi[k]);
-        P.half_f[k] = (float)(0.5 * (D->hi[k] - D->lo[k]));
+    if (D->kind == MCG_DOMAIN_BALL) {
+        if (!finite3(D->center) || !(D->radius > 0.0) || !std::isfinite(D->radius))
+            return set_error(MCG_ERR_ARG, "ball domain needs a finite centre and radius > 0");
+        P.ball = 1;
+        P.R = D->radius;
+        P.R2 = D->radius * D->radius;
+        P.R2_f = (float)P.R2;
+        for (int k = 0; k < 3; ++k) {
+            P.cen[k] = D->center[k];
+            P.lo[k] = D->center[k] - D->radius;  // bounding box
+            P.hi[k] = D->center[k] + D->radius;
+            P.half_f[k] = (float)D->radius;
+        }
+    } else if (D->kind == MCG_DOMAIN_BOX) {
+        if (!finite3(D->lo) || !finite3(D->hi)) return set_error(MCG_ERR_ARG, "domain bounds must be finite");
+        for (int k = 0; k < 3; ++k) {
+            if (!(D->lo[k] < D->hi[k])) return set_error(MCG_ERR_ARG, "domain lo[%d] >= hi[%d]", k, k);
+            P.lo[k] = D->lo[k];
+            P.hi[k] = D->hi[k];
+            P.cen[k] = 0.5 * (D->lo[k] + D->hi[k]);
+            P.half_f[k] = (float)(0.5 * (D->hi[k] - D->lo[k]));
+        }
+    } else {
+        return set_error(MCG_ERR_ARG, "unknown domain kind %d", D->kind);
     }
     if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(MCG_ERR_ARG, "dt must be positive and finite");
     if (!(o->sigma > 0.0) || !std::isfinite(o->sigma)) return set_error(MCG_ERR_ARG, "sigma must be positive");
@@ -125,6 +142,7 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     case MCG_G_TABLE:
         if (!B->faces || B->nu < 2 || B->nv < 2) return set_error(MCG_ERR_ARG, "tables need faces and nu, nv >= 2");
         if (!o->clip) return set_error(MCG_ERR_ARG, "tabulated boundary data needs clip = 1");
+        if (P.ball) return set_error(MCG_ERR_ARG, "tabulated boundary data needs the box domain");
         break;
     default:
         return set_error(MCG_ERR_ARG, "unknown boundary kind %d", B->kind);
@@ -144,6 +162,7 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     P.crn = o->crn_gz ? 1 : 0;
     P.clip = o->clip ? 1 : 0;
     P.bridge = o->bridge ? 1 : 0;
+    if (P.bridge && P.ball) return set_error(MCG_ERR_ARG, "the Brownian-bridge test needs the box domain");
     if (o->refill_min < 0 || o->refill_min > 32) return set_error(MCG_ERR_ARG, "refill_min must be in [0, 32]");
     P.refill_min = o->refill_min > 0 ? o->refill_min : 1;
     P.bridge_k = -2.0 / (P.sd * P.sd);
@@ -160,6 +179,10 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
         P.in_f[0] = (float)(P.half_f[0] - margin);
         P.in_f[1] = (float)(P.half_f[1] - margin);
         P.in_f[2] = (float)(P.half_f[2] - P.h - margin);
+        if (P.ball) {
+            const double rin = P.R - P.h - margin;
+            P.in_r2_f = rin > 0.0 ? (float)(rin * rin) : -1.0f;
+        }
         if (R->kind == MCG_RHO_PRISM) {
             for (int k = 0; k < 3; ++k) {
                 P.far_c[k] = (float)(0.5 * ((double)P.plo_f[k] + (double)P.phi_f[k]));
@@ -183,10 +206,16 @@ int check_station(const WalkParams& P, const double* x, int64_t s)
     const double off[3] = {0.0, P.h, -P.h};
     for (int c = 0; c < (P.crn ? 3 : 1); ++c) {
         const double y[3] = {x[0], x[1], x[2] + off[c]};
-        for (int k = 0; k < 3; ++k)
-            if (!(y[k] > P.lo[k] && y[k] < P.hi[k]))
-                return set_error(MCG_ERR_ARG, "station %lld (copy %d) is not strictly inside the domain",
-                                 (long long)s, c);
+        bool in = true;
+        if (P.ball) {
+            const double dx = y[0] - P.cen[0], dy = y[1] - P.cen[1], dz = y[2] - P.cen[2];
+            in = dx * dx + dy * dy + dz * dz < P.R2;
+        } else {
+            for (int k = 0; k < 3; ++k) in = in && y[k] > P.lo[k] && y[k] < P.hi[k];
+        }
+        if (!in)
+            return set_error(MCG_ERR_ARG, "station %lld (copy %d) is not strictly inside the domain", (long long)s,
+                             c);
     }
     return MCG_OK;
 }

@@ -13,7 +13,10 @@ namespace mcg {
 // (`cen`), so the exit test is |x_k| < half_k; the FP64 walk uses absolute
 // coordinates exactly as the problem states them.
 struct WalkParams {
-    // domain
+    // domain: the box (lo, hi), or the ball |x - cen| < R (ball = 1)
+    int32_t ball;
+    double R, R2;
+    float R2_f, in_r2_f;           // ball radius^2; all copies surely inside below in_r2_f
     double lo[3], hi[3], cen[3];
     float half_f[3];
     float in_f[3];                 // all three copies surely inside: |x_k| < in_f[k]

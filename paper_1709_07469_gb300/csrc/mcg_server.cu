@@ -52,6 +52,8 @@ struct mcg_request {
     char* dev = nullptr;
     size_t bytes = 0;
     int64_t round = 0;
+    int64_t done_paths = 0;   // paths per station merged so far
+    int64_t round_paths = 0;  // paths per station of the round in flight
     bool in_flight = false;
     cudaEvent_t ev = nullptr;
     double* h_res = nullptr;  // pinned: 6 S doubles + status word
@@ -126,17 +128,43 @@ void finish(mcg_request* r, int status, const char* msg)
     r->cv.notify_all();
 }
 
-// Launches round r->round of the request on its stream.
-int launch_round(mcg_server* sv, mcg_request* r)
+// Paths per station of the request's next round: one chunk until min_paths,
+// then the chunks the request's own spread says it still needs (90 % of the
+// estimate, at least one chunk, at most max_round_paths), never past
+// max_paths.  Depends only on the request's own results.
+int64_t next_round_paths(const mcg_server* sv, const mcg_request* r)
 {
     const int64_t chunk = sv->cfg.chunk_paths;
-    const Layout L = layout(r->S, chunk, sv->cfg.walk.precision);
+    int64_t m = 1;
+    if (r->done_paths >= sv->cfg.min_paths) {
+        double need = 0.0;
+        for (int64_t s = 0; s < r->S; ++s) {
+            const double u = r->h_res[s], se = r->h_res[2 * r->S + s];
+            const double sd = se * std::sqrt((double)r->done_paths);
+            const double n_s = (sd / (r->target * std::fabs(u))) * (sd / (r->target * std::fabs(u)));
+            if (std::isfinite(n_s) && n_s > need) need = n_s;
+        }
+        const double rest = 0.9 * (need - (double)r->done_paths);
+        if (rest > (double)chunk) m = (int64_t)std::ceil(rest / (double)chunk);
+        const int64_t mmax = sv->cfg.max_round_paths / chunk;
+        if (m > mmax) m = mmax;
+    }
+    int64_t n = m * chunk;
+    if (r->done_paths + n > sv->cfg.max_paths) n = sv->cfg.max_paths - r->done_paths;
+    return n > 0 ? n : chunk;
+}
+
+// Launches the request's next round on its stream.
+int launch_round(mcg_server* sv, mcg_request* r)
+{
+    const int64_t chunk = next_round_paths(sv, r);
+    const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
     cudaStream_t st = sv->streams[r->stream];
     WalkParams P = r->P;
     P.stations = (const double*)(r->dev + L.st);
     P.S = r->S;
     P.N = chunk;
-    P.p0 = r->round * chunk;
+    P.p0 = r->done_paths;
     P.total = (unsigned long long)r->S * (unsigned long long)chunk;
     P.pp_u = (double*)(r->dev + L.u);
     P.pp_d = (double*)(r->dev + L.d);
@@ -148,6 +176,7 @@ int launch_round(mcg_server* sv, mcg_request* r)
         P.frec = (float*)(r->dev + L.work);
         P.drec = (double*)(r->dev + L.work + align256(n * 3 * 8 * sizeof(float)));
     }
+    r->round_paths = chunk;
     mcg_station_state* states = (mcg_station_state*)(r->dev + L.states);
     double* res = (double*)(r->dev + L.res);
     cudaError_t e;
@@ -171,7 +200,7 @@ int admit(mcg_server* sv, mcg_request* r)
         if (sv->load[i] < sv->load[best]) best = i;
     r->stream = best;
     cudaStream_t st = sv->streams[best];
-    const Layout L = layout(r->S, sv->cfg.chunk_paths, sv->cfg.walk.precision);
+    const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
     cudaError_t e = cudaMallocAsync((void**)&r->dev, L.total, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -225,7 +254,7 @@ void scheduler(mcg_server* sv)
             // admission: FIFO, while the budget and the slot count allow
             while (!sv->pending.empty() && (int)sv->active.size() < sv->cfg.max_active) {
                 mcg_request* r = sv->pending.front();
-                const Layout L = layout(r->S, sv->cfg.chunk_paths, sv->cfg.walk.precision);
+                const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
                 if (!sv->active.empty() && sv->used + L.total > (size_t)sv->cfg.hbm_budget) break;
                 sv->pending.pop_front();
                 lk.unlock();
@@ -272,6 +301,7 @@ void scheduler(mcg_server* sv)
                 } else {
                     r->round++;
                     r->rounds.store(r->round);
+                    r->done_paths += r->round_paths;
                     int64_t n = 0;
                     std::memcpy(&n, r->h_res + 4 * r->S, sizeof(int64_t));
                     r->paths.store(n);
@@ -329,6 +359,7 @@ void mcg_server_config_default(mcg_server_config* c)
     c->chunk_paths = 4096;
     c->min_paths = 2 * 4096;
     c->max_paths = 10000000;
+    c->max_round_paths = 16 * 4096;
     mcg_options_default(&c->walk);
 }
 
@@ -394,6 +425,8 @@ int mcg_server_create(const mcg_server_config* cfg_in, mcg_server** out)
     if (cfg.max_active <= 0) return set_error(MCG_ERR_ARG, "max_active must be positive");
     if (cfg.chunk_paths <= 0 || cfg.max_paths < cfg.chunk_paths || cfg.hbm_budget <= 0)
         return set_error(MCG_ERR_ARG, "need chunk_paths > 0, max_paths >= chunk_paths, hbm_budget > 0");
+    if (cfg.max_round_paths < cfg.chunk_paths) cfg.max_round_paths = cfg.chunk_paths;
+    cfg.max_round_paths -= cfg.max_round_paths % cfg.chunk_paths;
     if (cfg.walk.precision != MCG_FP64 && cfg.walk.precision != MCG_MIXED)
         return set_error(MCG_ERR_ARG, "walk.precision must be MCG_FP64 or MCG_MIXED");
     mcg_server* sv = new mcg_server();

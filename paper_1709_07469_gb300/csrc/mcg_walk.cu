@@ -60,8 +60,15 @@ __device__ __forceinline__ bool refill(const WalkParams& P, bool busy, bool& exh
 __device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsigned long long item)
 {
     const double x = P.stations[3 * s], y = P.stations[3 * s + 1], z = P.stations[3 * s + 2];
-    const bool ok = x > P.lo[0] && x < P.hi[0] && y > P.lo[1] && y < P.hi[1] && z - P.h > P.lo[2] &&
-                    z + P.h < P.hi[2] && z > P.lo[2] && z < P.hi[2];
+    bool ok;
+    if (P.ball) {
+        const double dx = x - P.cen[0], dy = y - P.cen[1], dz = z - P.cen[2];
+        const double q = dx * dx + dy * dy;
+        ok = q + dz * dz < P.R2 && q + (dz + P.h) * (dz + P.h) < P.R2 && q + (dz - P.h) * (dz - P.h) < P.R2;
+    } else {
+        ok = x > P.lo[0] && x < P.hi[0] && y > P.lo[1] && y < P.hi[1] && z - P.h > P.lo[2] && z + P.h < P.hi[2] &&
+             z > P.lo[2] && z < P.hi[2];
+    }
     if (!ok) {
         P.pp_u[item] = kNaN;
         P.pp_d[item] = kNaN;
@@ -74,11 +81,32 @@ __device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsi
 
 __device__ __forceinline__ int64_t nstep_of(uint32_t blk, int m) { return 4 * (int64_t)blk + m + 1; }
 
+// The cancel flag may live in host-mapped or device memory and is written
+// by the host while the kernel runs: read it with a system-scope relaxed
+// load so the write is observed whatever caches the line.
 __device__ __forceinline__ bool cancelled(const WalkParams& P)
 {
     int c = 0;
-    if ((threadIdx.x & 31) == 0 && P.cancel != nullptr) c = *P.cancel;
+    if ((threadIdx.x & 31) == 0 && P.cancel != nullptr)
+        asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(c) : "l"((const void*)P.cancel) : "memory");
     return __shfl_sync(kFull, c, 0) != 0;
+}
+
+// Fraction theta in [0, 1] of the step X -> X + dW (coordinates relative to
+// the ball centre) at which the segment leaves the ball of radius R: the
+// positive root of |X + theta dW|^2 = R^2 in the form without cancellation.
+__device__ __forceinline__ double ball_theta(const double* q, const double* dW, double R2)
+{
+    double a = 0.0, b = 0.0, c = -R2;
+    for (int k = 0; k < 3; ++k) {
+        a = __dadd_rn(a, __dmul_rn(dW[k], dW[k]));
+        b = __dadd_rn(b, __dmul_rn(__dmul_rn(2.0, q[k]), dW[k]));
+        c = __dadd_rn(c, __dmul_rn(q[k], q[k]));
+    }
+    const double D = __dadd_rn(__dmul_rn(b, b), -__dmul_rn(__dmul_rn(4.0, a), c));
+    const double t = (b >= 0.0) ? __ddiv_rn(__dmul_rn(-2.0, c), __dadd_rn(b, __dsqrt_rn(D)))
+                                : __ddiv_rn(__dadd_rn(-b, __dsqrt_rn(D)), __dmul_rn(2.0, a));
+    return fmin(fmax(t, 0.0), 1.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -93,7 +121,11 @@ __device__ __noinline__ double exit_fp64(const WalkParams& P, const double* X, c
     double xs[3];
     double theta = 1.0;
     int face = -1;
-    if (P.clip) {
+    if (P.clip && P.ball) {
+        const double q[3] = {__dadd_rn(X[0], -P.cen[0]), __dadd_rn(X[1], -P.cen[1]), __dadd_rn(X[2], -P.cen[2])};
+        theta = ball_theta(q, dW, P.R2);
+        for (int k = 0; k < 3; ++k) xs[k] = __dadd_rn(X[k], __dmul_rn(theta, dW[k]));
+    } else if (P.clip) {
         int kstar = -1;
         double tmin = __longlong_as_double(0x7ff0000000000000LL), bstar = 0.0;
         for (int k = 0; k < 3; ++k) {
@@ -139,7 +171,10 @@ __device__ __forceinline__ double exit_mixed(const WalkParams& P, const float* X
     }
     double theta = 1.0;
     int face = -1;
-    if (P.clip) {
+    if (P.clip && P.ball) {
+        theta = ball_theta(X, dW, P.R2);
+        for (int k = 0; k < 3; ++k) xs[k] = P.cen[k] + (X[k] + theta * dW[k]);
+    } else if (P.clip) {
         int kstar = -1;
         double tmin = __longlong_as_double(0x7ff0000000000000LL);
         for (int k = 0; k < 3; ++k) {
@@ -327,8 +362,15 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
                 const double X[3] = {W[0], W[1], __dadd_rn(W[2], off[c])};
                 const double Y[3] = {Wn[0], Wn[1], __dadd_rn(Wn[2], off[c])};
                 steps += 1;
-                const bool inside = Y[0] > P.lo[0] && Y[0] < P.hi[0] && Y[1] > P.lo[1] && Y[1] < P.hi[1] &&
-                                    Y[2] > P.lo[2] && Y[2] < P.hi[2];
+                bool inside;
+                if (P.ball) {
+                    const double dx = __dadd_rn(Y[0], -P.cen[0]), dy = __dadd_rn(Y[1], -P.cen[1]),
+                                 dz = __dadd_rn(Y[2], -P.cen[2]);
+                    inside = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < P.R2;
+                } else {
+                    inside = Y[0] > P.lo[0] && Y[0] < P.hi[0] && Y[1] > P.lo[1] && Y[1] < P.hi[1] && Y[2] > P.lo[2] &&
+                             Y[2] < P.hi[2];
+                }
                 const int kb = (inside && P.bridge) ? bridge_face_f64(P, X, Y, s, p, (uint32_t)n) : -1;
                 if (inside && kb < 0) {
                     const double r = rho_f64(P, Y);
@@ -375,7 +417,7 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 // branch, so the slow double-precision unit sees one instruction per copy per
 // 64 steps).
 // ---------------------------------------------------------------------------
-template <int RHO, bool CRN, bool BRIDGE>
+template <int RHO, bool CRN, bool BRIDGE, bool BALL>
 __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
 {
     bool busy = false, exhausted = false;
@@ -427,7 +469,10 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     const float nx = wx + z[3 * m], ny = wy + z[3 * m + 1], nz = wz + z[3 * m + 2];
                     // common step: every copy surely inside Omega and surely
                     // outside the density's support -> nothing to do but move
-                    const bool inside_all = fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] && fabsf(nz) < P.in_f[2];
+                    const float qxy = BALL ? nx * nx + ny * ny : 0.0f;
+                    const bool inside_all = BALL ? qxy + nz * nz < P.in_r2_f
+                                                 : fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] &&
+                                                       fabsf(nz) < P.in_f[2];
                     bool no_rho = true;
                     if constexpr (RHO == MCG_RHO_PRISM) {
                         no_rho = !(fabsf(nx - P.far_c[0]) <= P.far_h[0] && fabsf(ny - P.far_c[1]) <= P.far_h[1] &&
@@ -446,11 +491,21 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                             zero_r = false;
                         }
                         if (!inside_all) {
-                            const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
-                            unsigned ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
-                            if (CRN) {
-                                ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
-                                ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
+                            unsigned ins;
+                            if (BALL) {
+                                const float za = nz, zb = nz + hf, zc = nz - hf;
+                                ins = (qxy + za * za < P.R2_f) ? 1u : 0u;
+                                if (CRN) {
+                                    ins |= (qxy + zb * zb < P.R2_f) ? 2u : 0u;
+                                    ins |= (qxy + zc * zc < P.R2_f) ? 4u : 0u;
+                                }
+                            } else {
+                                const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
+                                ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
+                                if (CRN) {
+                                    ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
+                                    ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
+                                }
                             }
                             const unsigned out = alive & ~ins;
                             if (out) {  // some copy left Omega on this step
@@ -551,10 +606,10 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
     }
 }
 
-template <int RHO, bool CRN, bool BRIDGE>
+template <int RHO, bool CRN, bool BRIDGE, bool BALL>
 cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t st)
 {
-    walk_mixed_kernel<RHO, CRN, BRIDGE><<<grid, block, 0, st>>>(P);
+    walk_mixed_kernel<RHO, CRN, BRIDGE, BALL><<<grid, block, 0, st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -569,16 +624,19 @@ cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t 
 template <int RHO>
 cudaError_t launch_mixed_rho(const WalkParams& P, int block, int grid, cudaStream_t st)
 {
-    if (P.crn) return P.bridge ? launch_mixed<RHO, true, true>(P, block, grid, st)
-                               : launch_mixed<RHO, true, false>(P, block, grid, st);
-    return P.bridge ? launch_mixed<RHO, false, true>(P, block, grid, st)
-                    : launch_mixed<RHO, false, false>(P, block, grid, st);
+    if (P.ball) return P.crn ? launch_mixed<RHO, true, false, true>(P, block, grid, st)
+                             : launch_mixed<RHO, false, false, true>(P, block, grid, st);
+    if (P.crn) return P.bridge ? launch_mixed<RHO, true, true, false>(P, block, grid, st)
+                               : launch_mixed<RHO, true, false, false>(P, block, grid, st);
+    return P.bridge ? launch_mixed<RHO, false, true, false>(P, block, grid, st)
+                    : launch_mixed<RHO, false, false, false>(P, block, grid, st);
 }
 
 template <int RHO>
 const void* mixed_fn(bool crn)
 {
-    return crn ? (const void*)walk_mixed_kernel<RHO, true, false> : (const void*)walk_mixed_kernel<RHO, false, false>;
+    return crn ? (const void*)walk_mixed_kernel<RHO, true, false, false>
+               : (const void*)walk_mixed_kernel<RHO, false, false, false>;
 }
 
 const void* kernel_fn(int precision, int rho_kind, bool crn)

@@ -18,6 +18,7 @@ from . import build as _build
 MCG_OK, MCG_ERR_ARG, MCG_ERR_OOM, MCG_ERR_CUDA = 0, 1, 2, 3
 MCG_ERR_STEP_CAP, MCG_ERR_TIMEOUT, MCG_ERR_NONFINITE, MCG_ERR_CANCELLED = 4, 5, 6, 7
 MCG_RHO_NONE, MCG_RHO_SPHERE, MCG_RHO_PRISM, MCG_RHO_VOXEL = 0, 1, 2, 3
+MCG_DOMAIN_BOX, MCG_DOMAIN_BALL = 0, 1
 MCG_G_ZERO, MCG_G_SPHERE, MCG_G_PRISM, MCG_G_TABLE, MCG_G_POLY = 0, 1, 2, 3, 4
 MCG_FP64, MCG_MIXED = 0, 1
 
@@ -28,7 +29,7 @@ D3 = C.c_double * 3
 
 
 class mcg_domain(C.Structure):
-    _fields_ = [("lo", D3), ("hi", D3)]
+    _fields_ = [("lo", D3), ("hi", D3), ("kind", C.c_int32), ("center", D3), ("radius", C.c_double)]
 
 
 class mcg_density(C.Structure):
@@ -57,7 +58,7 @@ class mcg_result(C.Structure):
 class mcg_server_config(C.Structure):
     _fields_ = [("streams", C.c_int32), ("max_active", C.c_int32), ("hbm_budget", C.c_int64),
                 ("chunk_paths", C.c_int64), ("min_paths", C.c_int64), ("max_paths", C.c_int64),
-                ("walk", mcg_options)]
+                ("max_round_paths", C.c_int64), ("walk", mcg_options)]
 
 
 class mcg_station_state(C.Structure):
@@ -203,7 +204,8 @@ class Problem:
 def problem(w, grid=None, faces=None) -> Problem:
     """C structures of a workload (paper_1709_07469_gb300.workloads.Workload).
     `grid` / `faces` are device tensors (float32) when the workload uses them."""
-    dom = mcg_domain(D3(*w.lo), D3(*w.hi))
+    dom = mcg_domain(D3(*w.lo), D3(*w.hi), 1 if getattr(w, "domain", "box") == "ball" else 0,
+                     D3(*getattr(w, "ball_center", (0.0, 0.0, 0.0))), getattr(w, "ball_radius", 0.0))
     den = mcg_density()
     den.kind = _RHO[w.rho_kind]
     den.G, den.rho0 = w.G, w.rho0
@@ -356,6 +358,8 @@ def server_config(opts: mcg_options | None = None, **kw) -> mcg_server_config:
         c.walk = opts
     for k, v in kw.items():
         setattr(c, k, v)
+    if "chunk_paths" in kw and "max_round_paths" not in kw:
+        c.max_round_paths = 16 * c.chunk_paths
     return c
 
 

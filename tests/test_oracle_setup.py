@@ -107,3 +107,15 @@ def test_table_nodes_reject_bad_index():
     spec = _spec(grid, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (-5.0,) * 3, (5.0,) * 3)
     with pytest.raises(ValueError):
         oracle.table_nodes(spec, [6], [0], [0], 4, 4)
+
+
+def test_voxel_field_equals_prism_closed_form_for_a_uniform_block():
+    grid = np.full((2, 2, 3), 400.0, dtype=np.float32)
+    origin, spacing = (-30.0, -20.0, -60.0), (20.0, 20.0, 25.0)
+    spec = _spec(grid, origin, spacing, (-500.0,) * 3, (500.0,) * 3)
+    pts = np.array([[0.0, 0.0, 10.0], [50.0, -70.0, -20.0], [5.0, 3.0, -40.0]])
+    phi, gz = oracle.voxel_field(spec, pts, want_gz=True)
+    hi = (origin[0] + 60.0, origin[1] + 40.0, origin[2] + 50.0)
+    for q, x in enumerate(pts):
+        assert abs(phi[q] - oracle.prism_phi(1.0, 400.0, origin, hi, x)) < 1e-10 * abs(phi[q])
+        assert abs(gz[q] - oracle.prism_gz(1.0, 400.0, origin, hi, x)) < 1e-9 * abs(gz[q]) + 1e-12
