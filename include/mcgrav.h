@@ -148,6 +148,8 @@ typedef struct {
                                 largest term, below Y, after a full step (default 0) */
     int32_t refill_min;      /* a warp refills its lanes once at least this many are
                                 free (1..32, default 1; mcg_autotune picks it)    */
+    int32_t graph;           /* mcgrav_solve with several batches: capture the batch
+                                sequence in one CUDA graph and launch it (default 1) */
 } mcg_options;
 
 /* Per-station outputs (caller-owned, length S; any pointer may be NULL). */

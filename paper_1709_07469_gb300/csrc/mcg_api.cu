@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -40,10 +41,29 @@ int set_error(int code, const char* fmt, ...)
 
 // Checks the problem description and fills the launch parameters (without
 // the work list, which the caller adds).
+void preload_kernels()
+{
+    static std::atomic<unsigned long long> loaded{0};  // one bit per device ordinal < 64
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (loaded.load(std::memory_order_acquire) & bit)) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (bit && (loaded.load(std::memory_order_relaxed) & bit)) return;
+    preload_walk_kernels();
+    preload_reduce_kernels();
+    loaded.fetch_or(bit, std::memory_order_release);
+}
+
 int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B, double dt, uint64_t seed,
                 const mcg_options* o, WalkParams& P)
 {
     if (!D || !R || !B || !o) return set_error(MCG_ERR_ARG, "null domain/density/boundary/options");
+    preload_kernels();
     std::memset(&P, 0, sizeof(P));
     if (D->kind == MCG_DOMAIN_BALL) {
         if (!finite3(D->center) || !(D->radius > 0.0) || !std::isfinite(D->radius))
@@ -299,6 +319,7 @@ void mcg_options_default(mcg_options* o)
     o->cancel = nullptr;
     o->bridge = 0;
     o->refill_min = 1;
+    o->graph = 1;
 }
 
 const char* mcg_last_error(void) { return g_err; }
@@ -367,6 +388,7 @@ int mcg_reduce(const double* pp_u, const double* pp_d, const int64_t* pp_steps, 
     if (S == 0 || N == 0) return MCG_OK;
     if (!pp_u || !pp_d || !pp_steps || !states_dev) return set_error(MCG_ERR_ARG, "null device buffer");
     if (S > 2147483647LL) return set_error(MCG_ERR_ARG, "too many stations for one reduction");
+    preload_kernels();
     cudaError_t e = launch_reduce(pp_u, pp_d, pp_steps, S, N, states_dev, (cudaStream_t)stream);
     return e == cudaSuccess ? MCG_OK : cuda_fail(e, "reduce kernel launch");
 }
@@ -377,6 +399,7 @@ int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double* u, doub
     if (S < 0) return set_error(MCG_ERR_ARG, "S must be non-negative");
     if (S == 0) return MCG_OK;
     if (!states_dev) return set_error(MCG_ERR_ARG, "null states");
+    preload_kernels();
     cudaError_t e = launch_finalize(states_dev, S, u, gz, se_u, se_gz, n_paths, path_steps, (cudaStream_t)stream);
     return e == cudaSuccess ? MCG_OK : cuda_fail(e, "finalize kernel launch");
 }
@@ -442,15 +465,54 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
             rc = cuda_fail(e, "workspace initialisation");
             break;
         }
+        // The batches (counter reset, walk, exit evaluation, reduction) and
+        // the finalize, in order on one stream.  With several batches and
+        // opts.graph the sequence is captured once into a CUDA graph and
+        // launched as one unit.
+        const bool use_graph = opts.graph && paths > batch;
+        cudaStream_t run = st;
+        if (use_graph) {
+            if ((e = cudaStreamCreateWithFlags(&run, cudaStreamNonBlocking)) ||
+                (e = cudaStreamBeginCapture(run, cudaStreamCaptureModeThreadLocal))) {
+                rc = cuda_fail(e, "graph capture");
+                break;
+            }
+        }
+        mcg_options ro = opts;
+        ro.stream = run;
         for (int64_t p0 = 0; p0 < paths && rc == MCG_OK; p0 += batch) {
             const int64_t nb = (paths - p0) < batch ? (paths - p0) : batch;
-            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &opts, d_u, d_d, d_steps, d_work,
+            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &ro, d_u, d_d, d_steps, d_work,
                           d_status, d_counter);
-            if (rc == MCG_OK) rc = mcg_reduce(d_u, d_d, d_steps, S, nb, d_state, st);
+            if (rc == MCG_OK) rc = mcg_reduce(d_u, d_d, d_steps, S, nb, d_state, run);
         }
-        if (rc) break;
-        rc = mcg_finalize(d_state, S, d_res, d_res + s_, d_res + 2 * s_, d_res + 3 * s_, (int64_t*)(d_res + 4 * s_),
-                          (int64_t*)(d_res + 5 * s_), st);
+        if (rc == MCG_OK)
+            rc = mcg_finalize(d_state, S, d_res, d_res + s_, d_res + 2 * s_, d_res + 3 * s_,
+                              (int64_t*)(d_res + 4 * s_), (int64_t*)(d_res + 5 * s_), run);
+        if (use_graph) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t ge = cudaStreamEndCapture(run, &graph);
+            if (rc == MCG_OK && ge == cudaSuccess) ge = cudaGraphInstantiate(&exec, graph, 0);
+            if (rc == MCG_OK && ge == cudaSuccess) {
+                // the graph runs after the initialisation already queued on st
+                cudaEvent_t ready;
+                ge = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+                if (ge == cudaSuccess) {
+                    cudaEventRecord(ready, st);
+                    cudaStreamWaitEvent(run, ready, 0);
+                    ge = cudaGraphLaunch(exec, run);
+                    cudaEventRecord(ready, run);
+                    cudaStreamWaitEvent(st, ready, 0);
+                    cudaEventDestroy(ready);
+                }
+            }
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamSynchronize(run);
+            cudaStreamDestroy(run);
+            if (rc == MCG_OK && ge != cudaSuccess) rc = cuda_fail(ge, "graph launch");
+        }
         if (rc) break;
         if ((e = cudaMemcpyAsync(h_res, d_res, 6 * s_ * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
             (e = cudaMemcpyAsync(&h_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||

@@ -82,6 +82,16 @@ int grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, double sigma_
 int boundary_tables(const mcg_domain* d, const mcg_density* rho, int32_t nu, int32_t nv, double near_cells,
                     float* faces_out, cudaStream_t st);
 
+// Loads every walk and reduction kernel of the library into the current
+// context (cudaFuncGetAttributes).  With CUDA's lazy module loading the first
+// launch of a kernel otherwise loads it on the spot, and that load waits for
+// the kernels already running on the device: a host thread that queues the
+// exit kernel behind a running walk would block until the walk ends.
+// preload_kernels() does it once per device (mcg_api.cu).
+void preload_walk_kernels();    // mcg_walk.cu
+void preload_reduce_kernels();  // mcg_reduce.cu
+void preload_kernels();
+
 // Thread-local error message (mcg_api.cu).
 int set_error(int code, const char* fmt, ...);
 

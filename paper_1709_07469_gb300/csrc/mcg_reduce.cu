@@ -124,6 +124,13 @@ __global__ void finalize_kernel(const mcg_station_state* __restrict__ states, in
 
 }  // namespace
 
+void preload_reduce_kernels()
+{
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, (const void*)reduce_kernel) != cudaSuccess) cudaGetLastError();
+    if (cudaFuncGetAttributes(&a, (const void*)finalize_kernel) != cudaSuccess) cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double* pp_u, const double* pp_d, const int64_t* pp_steps, int64_t S, int64_t N,
                           mcg_station_state* states, cudaStream_t st)
 {

@@ -652,6 +652,39 @@ const void* kernel_fn(int precision, int rho_kind, bool crn)
 
 }  // namespace
 
+namespace {
+
+template <typename K>
+void touch(K kernel)
+{
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, (const void*)kernel) != cudaSuccess) cudaGetLastError();
+}
+
+template <int RHO>
+void touch_mixed()
+{
+    touch(walk_mixed_kernel<RHO, true, false, true>);
+    touch(walk_mixed_kernel<RHO, false, false, true>);
+    touch(walk_mixed_kernel<RHO, true, true, false>);
+    touch(walk_mixed_kernel<RHO, true, false, false>);
+    touch(walk_mixed_kernel<RHO, false, true, false>);
+    touch(walk_mixed_kernel<RHO, false, false, false>);
+}
+
+}  // namespace
+
+void preload_walk_kernels()
+{
+    touch(walk_fp64_kernel<true>);
+    touch(walk_fp64_kernel<false>);
+    touch(exit_mixed_kernel);
+    touch_mixed<MCG_RHO_NONE>();
+    touch_mixed<MCG_RHO_SPHERE>();
+    touch_mixed<MCG_RHO_PRISM>();
+    touch_mixed<MCG_RHO_VOXEL>();
+}
+
 int walk_blocks_per_sm(int precision, int rho_kind, int block)
 {
     int nb = 0;

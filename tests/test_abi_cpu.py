@@ -64,6 +64,7 @@ def test_defaults_and_workspace(lib):
     lib.mcg_options_default(C.byref(o))
     assert o.h == 1e-2 and o.sigma == 1.0 and o.precision == M.MCG_MIXED and o.clip == 1 and o.crn_gz == 1
     assert o.max_steps == 1 << 31
+    assert o.graph == 1 and o.refill_min == 1 and o.bridge == 0
     assert M.mcg_workspace_bytes(0, 10) == 0
     b = M.mcg_workspace_bytes(30, 1000)
     # per path: u, d, steps (24 B) + the mixed walk's exit records (3 x 40 B)

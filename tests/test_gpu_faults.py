@@ -3,7 +3,10 @@
 * Cancellation: a device flag that the walk polls, written by an
   asynchronous copy on another stream while a long walk runs: the kernel
   stops taking work, returns promptly and reports MCG_ERR_CANCELLED (no trap,
-  no abandoned wait).
+  no abandoned wait).  It runs first in a fresh process on purpose: the
+  library loads its kernels before the first launch, so queueing the exit
+  kernel behind the running walk does not block the host until the walk
+  ends (what CUDA's lazy module loading would otherwise do).
 * Non-finite data (a NaN in the boundary tables) reaches the status word as
   MCG_ERR_NONFINITE; the step cap as MCG_ERR_STEP_CAP.
 * Checkpoint / resume: station states (64 bytes each) saved after half the

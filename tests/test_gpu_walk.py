@@ -322,3 +322,14 @@ def test_paper_experiment_1_line():
     rel_offset = off / np.abs(phi)
     assert np.all((rel_offset > 0.008) & (rel_offset < 0.03))     # the paper's "around 1 %"
     assert np.all(np.abs(r["u"] - (phi + off)) < 4 * r["se_u"] + 0.01 * np.abs(phi))
+
+
+def test_mcgrav_solve_graph_equals_stream_launches():
+    """Several batches captured into one CUDA graph give the same numbers as
+    the same launches issued on the stream."""
+    w = W.sphere_line(paths=6000)
+    prob = M.problem(w)
+    a = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=1000, graph=1))
+    b = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=1000, graph=0))
+    for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
