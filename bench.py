@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=32768, help="paths per station per step")
+    ap.add_argument("--block", type=int, default=0, help="threads per block of the walk (0: library default)")
+    ap.add_argument("--migrate", type=int, default=1, choices=[0, 1],
+                    help="hand the last walks of sparse warps to warps with free lanes (default 1)")
     ap.add_argument("--cpu-paths", type=int, default=48, help="paths per station in the CPU-oracle sample")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
@@ -223,7 +226,7 @@ def run_ours(args):
     status = torch.zeros(2, dtype=torch.int32, device=dev)
     res = torch.empty((6, S), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    opts = [M.options(w, precision=M.MCG_MIXED, stream=s) for s in streams]
+    opts = [M.options(w, precision=M.MCG_MIXED, stream=s, block=args.block, migrate=args.migrate) for s in streams]
 
     def path_block(j):
         # step j of this rank takes paths [p0, p0 + Bp) of every station (wrapping)
@@ -365,7 +368,7 @@ def _sum_op(world):
     return dist.ReduceOp.SUM
 
 
-def fp64_comparison(M, w, dev):
+def fp64_comparison(M, w, dev, block=0):
     """Stepping rate of the plain FP64 walk and of the mixed walk on the same
     workload, free of exit-time tails: every path runs exactly `cap` RNG-steps
     (max_steps), so all lanes stay busy for the whole launch."""
@@ -374,7 +377,7 @@ def fp64_comparison(M, w, dev):
     out = {}
     for name, prec, batch, cap in (("fp64", M.MCG_FP64, 4096, 256), ("mixed", M.MCG_MIXED, 8192, 16384)):
         from paper_1709_07469_gb300.device import DeviceSolve
-        ds = DeviceSolve(w, batch=batch, precision=prec)
+        ds = DeviceSolve(w, batch=batch, precision=prec, block=block)
         ds.opts.max_steps = cap
         ds.reset()
         ds.walk(10**5)
@@ -615,7 +618,7 @@ def main():
         from paper_1709_07469_gb300 import workloads as W
         B.build()
         M.load()
-        print(json.dumps(fp64_comparison(M, W.prism_ore_body(), torch.device("cuda", 0))), flush=True)
+        print(json.dumps(fp64_comparison(M, W.prism_ore_body(), torch.device("cuda", 0), args.block)), flush=True)
         return 0
     return run_ours(args)
 

@@ -150,6 +150,12 @@ typedef struct {
                                 free (1..32, default 1; mcg_autotune picks it)    */
     int32_t graph;           /* mcgrav_solve with several batches: capture the batch
                                 sequence in one CUDA graph and launch it (default 1) */
+    int32_t migrate;         /* mixed walk: once the work list is used up, warps with
+                                few walks left hand them to warps with free lanes
+                                through a pool in work_dev (default 1).  Results do
+                                not depend on it for piecewise-constant densities;
+                                for a voxel grid the single-precision partial sums
+                                are flushed at other steps (rounding only).       */
 } mcg_options;
 
 /* Per-station outputs (caller-owned, length S; any pointer may be NULL). */
@@ -205,8 +211,10 @@ MCG_API int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, c
  *   stations_dev: DEVICE, S x 3.   pp_*: DEVICE, length S*N.
  *   work_dev    : DEVICE scratch of mcg_walk_work_bytes(S, N, precision)
  *                 bytes (the mixed walk stores each copy's exit record
- *                 there and a second kernel evaluates the exits); may be
- *                 NULL when that size is 0.  Caller-owned, 256-byte aligned.
+ *                 there and a second kernel evaluates the exits; it also
+ *                 holds the migration pool and its counters, reset by this
+ *                 call); may be NULL when that size is 0.  Caller-owned,
+ *                 256-byte aligned.
  *   status_dev  : DEVICE int32, OR-ed with (1 << status) for every path that
  *                 hit the step cap, started outside Omega or produced a
  *                 non-finite value; the caller zeroes it.
@@ -239,6 +247,8 @@ MCG_API size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision);
  *   - All calls share the one array and it keeps the last call's contents;
  *     the call zeroes the counter itself.  Calls that overlap on the GPU
  *     (other streams, other threads) race on it: serialise them.
+ *   - opts->migrate is ignored: the array holds no migration pool, so each
+ *     warp keeps its walks to the end (same results, longer exit-time tail).
  * Asynchronous on opts->stream like mcg_walk. */
 MCG_API int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
                             const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,

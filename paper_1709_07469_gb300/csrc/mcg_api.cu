@@ -59,6 +59,55 @@ void preload_kernels()
     loaded.fetch_or(bit, std::memory_order_release);
 }
 
+WorkLayout work_layout(size_t n)
+{
+    WorkLayout L;
+    L.cap = n < kPoolMaxSlots ? (unsigned long long)n : kPoolMaxSlots;
+    size_t o = 0;
+    L.frec = o;
+    o += align256(n * 3 * 8 * sizeof(float));
+    L.drec = o;
+    o += align256(n * 3 * sizeof(double));
+    L.pool = o;
+    o += align256((size_t)L.cap * kPoolEntryBytes);
+    L.ready = o;
+    o += align256((size_t)L.cap * sizeof(uint32_t));
+    L.ctr = o;
+    o += 256;
+    L.total = o;
+    return L;
+}
+
+void bind_work(WalkParams& P, void* work, bool migrate)
+{
+    const WorkLayout L = work_layout((size_t)P.total);
+    unsigned char* w = (unsigned char*)work;
+    P.frec = (float*)(w + L.frec);
+    P.drec = (double*)(w + L.drec);
+    if (migrate && L.cap > 0) {
+        P.pool = w + L.pool;
+        P.pool_ready = (uint32_t*)(w + L.ready);
+        P.pool_ctr = (unsigned long long*)(w + L.ctr);
+        P.pool_cap = L.cap;
+    } else {
+        P.pool = nullptr;
+        P.pool_ready = nullptr;
+        P.pool_ctr = nullptr;
+        P.pool_cap = 0;
+    }
+}
+
+cudaError_t reset_walk(const WalkParams& P, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && P.pool) {
+        // flags and counters are adjacent: one memset covers both
+        const size_t bytes = (size_t)((unsigned char*)P.pool_ctr - (unsigned char*)P.pool_ready) + 256;
+        e = cudaMemsetAsync(P.pool_ready, 0, bytes, st);
+    }
+    return e;
+}
+
 int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B, double dt, uint64_t seed,
                 const mcg_options* o, WalkParams& P)
 {
@@ -320,6 +369,7 @@ void mcg_options_default(mcg_options* o)
     o->bridge = 0;
     o->refill_min = 1;
     o->graph = 1;
+    o->migrate = 1;
 }
 
 const char* mcg_last_error(void) { return g_err; }
@@ -338,8 +388,7 @@ size_t mcg_workspace_bytes(int64_t S, int64_t batch)
 size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision)
 {
     if (S <= 0 || N <= 0 || precision != MCG_MIXED) return 0;
-    const size_t n = (size_t)S * (size_t)N;
-    return align256(n * 3 * 8 * sizeof(float)) + align256(n * 3 * sizeof(double));
+    return work_layout((size_t)S * (size_t)N).total;
 }
 
 int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
@@ -369,13 +418,11 @@ int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_bou
     if (opts->precision == MCG_MIXED) {
         if (!work_dev) return set_error(MCG_ERR_ARG, "the mixed walk needs work_dev (mcg_walk_work_bytes)");
         if ((uintptr_t)work_dev % 256 != 0) return set_error(MCG_ERR_ARG, "work_dev must be 256-byte aligned");
-        const size_t n = (size_t)S * (size_t)N;
-        P.frec = (float*)work_dev;
-        P.drec = (double*)((char*)work_dev + align256(n * 3 * 8 * sizeof(float)));
+        bind_work(P, work_dev, opts->migrate != 0);
     }
     cudaStream_t st = (cudaStream_t)opts->stream;
-    cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+    cudaError_t e = reset_walk(P, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
     e = launch_walk(P, opts->precision, opts->block ? opts->block : 128, st);
     if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     return MCG_OK;

@@ -59,7 +59,30 @@ struct WalkParams {
     float* frec;                   // mixed walk: exit records (8 floats per copy per item)
     double* drec;                  // mixed walk: flushed sums per copy per item
     volatile int32_t* cancel;
+    // mixed walk, migration of walks between warps once the work list is used
+    // up (null pool: off).  pool: kPoolEntryBytes per slot; pool_ready: one
+    // flag per slot; pool_ctr: [0] slots reserved, [1] slots claimed, [2]
+    // warps gone.
+    unsigned char* pool;
+    uint32_t* pool_ready;
+    unsigned long long* pool_ctr;
+    unsigned long long pool_cap;
 };
+
+constexpr size_t kPoolEntryBytes = 80;
+constexpr unsigned long long kPoolMaxSlots = 1ull << 19;
+
+// Offsets inside the mixed walk's scratch of n = S * N items (mcg_api.cu):
+// exit records, flushed sums, migration pool, ready flags, pool counters.
+struct WorkLayout {
+    size_t frec, drec, pool, ready, ctr, total;
+    unsigned long long cap;
+};
+WorkLayout work_layout(size_t n);
+// Points P's mixed-walk buffers into `work` (layout above); migration on/off.
+void bind_work(WalkParams& P, void* work, bool migrate);
+// Zeroes the work counter and, with migration, the pool's flags and counters.
+cudaError_t reset_walk(const WalkParams& P, cudaStream_t st);
 
 // Kernel launchers (mcg_walk.cu).
 cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStream_t st);

@@ -171,16 +171,12 @@ int launch_round(mcg_server* sv, mcg_request* r)
     P.pp_steps = (int64_t*)(r->dev + L.steps);
     P.status = (int32_t*)(r->dev + L.status);
     P.counter = (unsigned long long*)(r->dev + L.status + 128);
-    if (sv->cfg.walk.precision == MCG_MIXED) {
-        const size_t n = (size_t)P.total;
-        P.frec = (float*)(r->dev + L.work);
-        P.drec = (double*)(r->dev + L.work + align256(n * 3 * 8 * sizeof(float)));
-    }
+    if (sv->cfg.walk.precision == MCG_MIXED) bind_work(P, r->dev + L.work, sv->cfg.walk.migrate != 0);
     r->round_paths = chunk;
     mcg_station_state* states = (mcg_station_state*)(r->dev + L.states);
     double* res = (double*)(r->dev + L.res);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st)) ||
+    if ((e = reset_walk(P, st)) ||
         (e = launch_walk(P, sv->cfg.walk.precision, sv->cfg.walk.block ? sv->cfg.walk.block : 128, st)) ||
         (e = launch_reduce(P.pp_u, P.pp_d, P.pp_steps, r->S, chunk, states, st)) ||
         (e = launch_finalize(states, r->S, res, res + r->S, res + 2 * r->S, res + 3 * r->S, (int64_t*)(res + 4 * r->S),

@@ -92,6 +92,99 @@ __device__ __forceinline__ bool cancelled(const WalkParams& P)
     return __shfl_sync(kFull, c, 0) != 0;
 }
 
+// ---------------------------------------------------------------------------
+// Migration of walks between warps (mixed walk).  Once the work list is used
+// up, a warp's lanes empty one by one as its walks exit, and a warp with a
+// few long walks left would keep issuing instructions for 32 lanes to the
+// end.  Such a warp (at most kSpillMax walks live, migration on) writes its
+// walks to the pool and leaves; warps with free lanes claim pooled walks.
+// A walk's state is all of it: the random streams are keyed by (station,
+// path, step), so where a walk continues does not change its numbers.
+//   reserve: CAS on pool_ctr[0] below pool_cap; entries written, then the
+//            slot's ready flag set with release semantics;
+//   claim  : CAS on pool_ctr[1] below pool_ctr[0]; acquire on the ready flag
+//            (a bounded wait: the producer is a running warp between its
+//            reservation and its store, so the flag comes);
+//   leave  : a warp with no walks adds 1 to pool_ctr[2]; the last warp to
+//            leave (count = all warps of the grid) sees every earlier spill
+//            and, if the pool still holds walks, takes them over.
+// Each warp spills at most once, so slots are never reused.
+// ---------------------------------------------------------------------------
+#ifndef MCG_SPILL_MAX
+#define MCG_SPILL_MAX 8
+#endif
+#ifndef MCG_SPILL_BACKLOG
+#define MCG_SPILL_BACKLOG 64
+#endif
+constexpr int kSpillMax = MCG_SPILL_MAX;               // spill a warp with at most this many walks
+constexpr unsigned long long kSpillBacklog = MCG_SPILL_BACKLOG;  // ... while fewer pooled walks wait
+constexpr int kReadySpin = 1 << 20;                   // bounded wait for a ready flag (~0.1 s)
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* a)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* a)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* a, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// Leader: claims up to `want` pooled walks; returns the count, first slot in base.
+__device__ __forceinline__ unsigned pool_take(const WalkParams& P, unsigned want, unsigned long long& base)
+{
+    for (int t = 0; t < 32; ++t) {
+        const unsigned long long r = ld_acquire_u64(P.pool_ctr);
+        const unsigned long long c = ld_acquire_u64(P.pool_ctr + 1);
+        if (c >= r) return 0u;
+        const unsigned long long k = (r - c) < want ? (r - c) : want;
+        if (atomicCAS(P.pool_ctr + 1, c, c + k) == c) {
+            base = c;
+            return (unsigned)k;
+        }
+    }
+    return 0u;
+}
+
+// Leader: reserves n slots if the pool has room and few walks wait there.
+__device__ __forceinline__ bool pool_reserve(const WalkParams& P, unsigned n, unsigned long long& base)
+{
+    for (int t = 0; t < 32; ++t) {
+        const unsigned long long r = ld_acquire_u64(P.pool_ctr);
+        const unsigned long long c = ld_acquire_u64(P.pool_ctr + 1);
+        if (r - c >= kSpillBacklog || r + n > P.pool_cap) return false;
+        if (atomicCAS(P.pool_ctr, r, r + n) == r) {
+            base = r;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Leader: records that this warp has no walks.  Returns false when it was
+// the last warp of the grid to leave and walks are still pooled: it must
+// take them over.
+__device__ __forceinline__ bool pool_leave(const WalkParams& P, bool stop)
+{
+    __threadfence();
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long prev = atomicAdd(P.pool_ctr + 2, 1ull);
+    if (stop || prev + 1ull != warps) return true;
+    __threadfence();
+    if (ld_acquire_u64(P.pool_ctr + 1) < ld_acquire_u64(P.pool_ctr)) {
+        atomicAdd(P.pool_ctr + 2, ~0ull);  // -1: still here
+        return false;
+    }
+    return true;
+}
+
 // Fraction theta in [0, 1] of the step X -> X + dW (coordinates relative to
 // the ball centre) at which the segment leaves the ball of radius R: the
 // positive root of |X + theta dW|^2 = R^2 in the form without cancellation.
@@ -433,12 +526,18 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
     const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2];
     const float hf = CRN ? P.h_f : 0.0f;
     unsigned round = 0u;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const bool migrate = P.pool != nullptr;
+    bool stop = false;     // cancelled: take no more work of any kind
+    bool spilled = false;  // this warp has spilled its walks once
 
     for (;;) {
         if ((++round & 15u) == 0u && cancelled(P)) {
             if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
             busy = false;
             exhausted = true;
+            stop = true;
         }
         if (refill(P, busy, exhausted, item) &&
             station_ok(P, s = (uint32_t)(item / (unsigned long long)P.N), item)) {
@@ -457,7 +556,88 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             zero_r = false;
             busy = true;
         }
-        if (!__any_sync(kFull, busy)) break;
+        if (migrate && !stop) {
+            // the work list is used up: fill free lanes with pooled walks
+            const unsigned freem = __ballot_sync(kFull, !busy);
+            if (freem && __any_sync(kFull, exhausted)) {
+                unsigned long long base = 0ull;
+                unsigned got = 0u;
+                if (lane == 0) got = pool_take(P, (unsigned)__popc(freem), base);
+                got = __shfl_sync(kFull, got, 0);
+                base = __shfl_sync(kFull, base, 0);
+                const unsigned rank = (unsigned)__popc(freem & lanes_below);
+                if (!busy && rank < got) {
+                    const unsigned long long slot = base + rank;
+                    uint32_t ready = 0u;
+                    for (int i = 0; i < kReadySpin && !ready; ++i) {
+                        ready = ld_acquire_u32(P.pool_ready + slot);
+                        if (!ready) __nanosleep(64);
+                    }
+                    if (ready) {
+                        const uint4* e = (const uint4*)(P.pool + slot * kPoolEntryBytes);
+                        const uint4 e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3], e4 = e[4];
+                        item = ((unsigned long long)e0.y << 32) | e0.x;
+                        s = (uint32_t)(item / (unsigned long long)P.N);
+                        p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
+                        blk = e0.z;
+                        alive = e0.w;
+                        wx = __uint_as_float(e1.x);
+                        wy = __uint_as_float(e1.y);
+                        wz = __uint_as_float(e1.z);
+                        r0 = __uint_as_float(e1.w);
+                        r1 = __uint_as_float(e2.x);
+                        r2 = __uint_as_float(e2.y);
+                        steps = (int64_t)(((unsigned long long)e2.w << 32) | e2.z);
+                        D0 = __hiloint2double((int)e3.y, (int)e3.x);
+                        D1 = __hiloint2double((int)e3.w, (int)e3.z);
+                        D2 = __hiloint2double((int)e4.y, (int)e4.x);
+                        S0 = S1 = S2 = 0.f;
+                        zero_r = false;
+                        busy = true;
+                    } else {
+                        atomicOr(P.status, 1 << MCG_ERR_TIMEOUT);
+                    }
+                }
+            }
+        }
+        unsigned livem = __ballot_sync(kFull, busy);
+        if (migrate && !stop && !spilled && livem != 0u && __popc(livem) <= kSpillMax &&
+            __any_sync(kFull, exhausted)) {
+            // few walks left here and nothing new to start: hand them over
+            unsigned long long base = 0ull;
+            int ok = 0;
+            if (lane == 0) ok = pool_reserve(P, (unsigned)__popc(livem), base) ? 1 : 0;
+            if (__shfl_sync(kFull, ok, 0)) {
+                base = __shfl_sync(kFull, base, 0);
+                if (busy) {
+                    const unsigned long long slot = base + (unsigned)__popc(livem & lanes_below);
+                    D0 += (double)S0;
+                    D1 += (double)S1;
+                    D2 += (double)S2;
+                    const float q0 = zero_r ? 0.f : r0, q1 = zero_r ? 0.f : r1, q2 = zero_r ? 0.f : r2;
+                    uint4* e = (uint4*)(P.pool + slot * kPoolEntryBytes);
+                    e[0] = make_uint4((uint32_t)item, (uint32_t)(item >> 32), blk, alive);
+                    e[1] = make_uint4(__float_as_uint(wx), __float_as_uint(wy), __float_as_uint(wz),
+                                      __float_as_uint(q0));
+                    e[2] = make_uint4(__float_as_uint(q1), __float_as_uint(q2), (uint32_t)(unsigned long long)steps,
+                                      (uint32_t)((unsigned long long)steps >> 32));
+                    e[3] = make_uint4((uint32_t)__double2loint(D0), (uint32_t)__double2hiint(D0),
+                                      (uint32_t)__double2loint(D1), (uint32_t)__double2hiint(D1));
+                    e[4] = make_uint4((uint32_t)__double2loint(D2), (uint32_t)__double2hiint(D2), 0u, 0u);
+                    st_release_u32(P.pool_ready + slot, 1u);
+                    busy = false;
+                }
+                spilled = true;
+                livem = 0u;
+            }
+        }
+        if (livem == 0u) {
+            if (!migrate) break;
+            int leave = 1;
+            if (lane == 0) leave = pool_leave(P, stop) ? 1 : 0;
+            if (__shfl_sync(kFull, leave, 0)) break;
+            continue;  // the last warp: take over the pooled walks
+        }
 
 #pragma unroll 1
         for (int k = 0; k < 16; ++k) {

@@ -47,7 +47,8 @@ class mcg_options(C.Structure):
     _fields_ = [("h", C.c_double), ("sigma", C.c_double), ("precision", C.c_int32), ("clip", C.c_int32),
                 ("crn_gz", C.c_int32), ("block", C.c_int32), ("max_steps", C.c_int64),
                 ("batch_paths", C.c_int64), ("stream", C.c_void_p), ("cancel", C.c_void_p),
-                ("bridge", C.c_int32), ("refill_min", C.c_int32), ("graph", C.c_int32)]
+                ("bridge", C.c_int32), ("refill_min", C.c_int32), ("graph", C.c_int32),
+                ("migrate", C.c_int32)]
 
 
 class mcg_result(C.Structure):

@@ -64,13 +64,17 @@ def test_defaults_and_workspace(lib):
     lib.mcg_options_default(C.byref(o))
     assert o.h == 1e-2 and o.sigma == 1.0 and o.precision == M.MCG_MIXED and o.clip == 1 and o.crn_gz == 1
     assert o.max_steps == 1 << 31
-    assert o.graph == 1 and o.refill_min == 1 and o.bridge == 0
+    assert o.graph == 1 and o.refill_min == 1 and o.bridge == 0 and o.migrate == 1
     assert M.mcg_workspace_bytes(0, 10) == 0
     b = M.mcg_workspace_bytes(30, 1000)
     # per path: u, d, steps (24 B) + the mixed walk's exit records (3 x 40 B)
-    assert b >= 30 * 1000 * 144 and b < 30 * 1000 * 144 + 64 * 1024
+    # + a migration-pool slot (80 B) and its ready flag (4 B)
+    assert b >= 30 * 1000 * 228 and b < 30 * 1000 * 228 + 64 * 1024
     assert M.mcg_walk_work_bytes(30, 1000, M.MCG_FP64) == 0
-    assert M.mcg_walk_work_bytes(30, 1000, M.MCG_MIXED) >= 30 * 1000 * 120
+    assert M.mcg_walk_work_bytes(30, 1000, M.MCG_MIXED) >= 30 * 1000 * 204
+    # the pool stops growing at 2^19 slots
+    big = M.mcg_walk_work_bytes(1000, 10_000, M.MCG_MIXED)
+    assert big >= 10**7 * 120 + (1 << 19) * 84 and big < 10**7 * 120 + (1 << 19) * 84 + 64 * 1024
     assert "sm_103a" in M.version()
 
 

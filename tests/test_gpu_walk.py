@@ -333,3 +333,53 @@ def test_mcgrav_solve_graph_equals_stream_launches():
     b = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=1000, graph=0))
     for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps"):
         assert np.array_equal(getattr(a, k), getattr(b, k)), k
+
+
+def _per_path_migrate(w, migrate, **kw):
+    ds = DeviceSolve(w, precision=M.MCG_MIXED, **kw)
+    ds.opts.migrate = migrate
+    ds.reset()
+    ds.work.fill_(255)   # stale pool flags must not read as ready
+    ds.walk(0)
+    u, d, st = ds.per_path()
+    return u, d, st, int(ds.status[0].item())
+
+
+@pytest.mark.parametrize("name,w", [
+    # fewer walks than lanes: the work list is used up at once and warps spill from the start
+    ("prism, 30 x 512", W.prism_ore_body(paths=512)),
+    # a few walks per lane, then the exit-time tail
+    ("prism, 30 x 8192", W.prism_ore_body(paths=8192)),
+    # less than one warp of work, and a ragged count
+    ("prism, 3 x 7", W.prism_ore_body(paths=7).with_(stations=W.prism_ore_body().stations[:3])),
+    ("sphere, 8 x 20000", W.sphere_line(paths=20000)),
+])
+def test_migration_leaves_every_path_unchanged(name, w):
+    """Walks handed between warps keep their numbers: with a piecewise-constant
+    density the partial sums are exact, so every per-path value is bit-identical
+    with and without migration."""
+    a = _per_path_migrate(w, 1)
+    b = _per_path_migrate(w, 0)
+    assert a[3] == 0 and b[3] == 0
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    assert np.all(np.isfinite(a[0])) and np.all(a[2] > 0)
+
+
+def test_migration_voxel_rounding_only():
+    """Voxel density: migration moves the flush points of the single-precision
+    partial sums, which changes u by rounding only; exit steps are identical.
+    A flush of up to 64 single-precision terms carries a relative error of at
+    most 64 * 2^-24 ~ 4e-6 of the source integral, whose term in u is below
+    max |u| here; the allowance is 4e-6 max |u|, absolute (u itself can be
+    near zero where g and the integral cancel)."""
+    from tests.helpers import smooth_tables
+    w = W.voxel_survey(shape=(32, 32, 16), table_n=(33, 33), paths=256, n_side=8)
+    grid = torch.from_numpy(oracle.grf_density(1, 32, 32, 16, sigma_vox=2.0, amp=300.0)).cuda()
+    faces = torch.from_numpy(smooth_tables(w, scale=-1e-4)).cuda()
+    a = _per_path_migrate(w, 1, grid=grid, faces=faces)
+    b = _per_path_migrate(w, 0, grid=grid, faces=faces)
+    assert a[3] == 0 and b[3] == 0
+    assert np.array_equal(a[2], b[2])
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=4e-6 * np.abs(b[0]).max())
+    assert np.mean(a[0] == b[0]) > 0.2   # paths that never migrated are bit-identical
