@@ -129,57 +129,36 @@ __device__ __forceinline__ void normals12_f32(uint32_t s, uint32_t p, uint32_t b
 // ---------------------------------------------------------------------------
 // Density samplers.
 // ---------------------------------------------------------------------------
-template <int RHO>
-__device__ __forceinline__ float rho_f32(const WalkParams& P, float x, float y, float z)
-{
-    if constexpr (RHO == MCG_RHO_SPHERE) {
-        const float dx = x - P.sc_f[0], dy = y - P.sc_f[1], dz = z - P.sc_f[2];
-        return (dx * dx + dy * dy + dz * dz < P.srad2_f) ? P.rho0_f : 0.0f;
-    } else if constexpr (RHO == MCG_RHO_PRISM) {
-        const bool in = x >= P.plo_f[0] && x < P.phi_f[0] && y >= P.plo_f[1] && y < P.phi_f[1] &&
-                        z >= P.plo_f[2] && z < P.phi_f[2];
-        return in ? P.rho0_f : 0.0f;
-    } else if constexpr (RHO == MCG_RHO_VOXEL) {
-        const float tx = floorf((x - P.org_f[0]) * P.inv_sp_f[0]);
-        const float ty = floorf((y - P.org_f[1]) * P.inv_sp_f[1]);
-        const float tz = floorf((z - P.org_f[2]) * P.inv_sp_f[2]);
-        const bool in = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny && tz >= 0.f &&
-                        tz < (float)P.nz;
-        if (!in) return 0.0f;
-        const int idx = (int)tx + P.nx * ((int)ty + P.ny * (int)tz);
-        return __ldg(P.grid + idx);
-    } else {
-        return 0.0f;
-    }
-}
-
 // Density at the three common-random-number copies (x, y, z), (x, y, z+h),
-// (x, y, z-h): the x / y part is computed once.
+// (x, y, z-h): the x / y part is computed once.  Every rounding step is
+// explicit (no contraction left to the compiler), so the walk kernel and the
+// exit kernel, which re-evaluates rho at the last inside point, agree bit for
+// bit.
 template <int RHO>
 __device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, float z, float h, float& ra,
                                          float& rb, float& rc)
 {
     if constexpr (RHO == MCG_RHO_SPHERE) {
-        const float dx = x - P.sc_f[0], dy = y - P.sc_f[1], dz = z - P.sc_f[2];
-        const float q = dx * dx + dy * dy;
-        const float za = dz, zb = dz + h, zc = dz - h;
-        ra = (q + za * za < P.srad2_f) ? P.rho0_f : 0.0f;
-        rb = (q + zb * zb < P.srad2_f) ? P.rho0_f : 0.0f;
-        rc = (q + zc * zc < P.srad2_f) ? P.rho0_f : 0.0f;
+        const float dx = __fsub_rn(x, P.sc_f[0]), dy = __fsub_rn(y, P.sc_f[1]), dz = __fsub_rn(z, P.sc_f[2]);
+        const float q = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        const float za = dz, zb = __fadd_rn(dz, h), zc = __fsub_rn(dz, h);
+        ra = (__fmaf_rn(za, za, q) < P.srad2_f) ? P.rho0_f : 0.0f;
+        rb = (__fmaf_rn(zb, zb, q) < P.srad2_f) ? P.rho0_f : 0.0f;
+        rc = (__fmaf_rn(zc, zc, q) < P.srad2_f) ? P.rho0_f : 0.0f;
     } else if constexpr (RHO == MCG_RHO_PRISM) {
         const bool inxy = x >= P.plo_f[0] && x < P.phi_f[0] && y >= P.plo_f[1] && y < P.phi_f[1];
-        const float zb = z + h, zc = z - h;
+        const float zb = __fadd_rn(z, h), zc = __fsub_rn(z, h);
         ra = (inxy && z >= P.plo_f[2] && z < P.phi_f[2]) ? P.rho0_f : 0.0f;
         rb = (inxy && zb >= P.plo_f[2] && zb < P.phi_f[2]) ? P.rho0_f : 0.0f;
         rc = (inxy && zc >= P.plo_f[2] && zc < P.phi_f[2]) ? P.rho0_f : 0.0f;
     } else if constexpr (RHO == MCG_RHO_VOXEL) {
-        const float tx = floorf((x - P.org_f[0]) * P.inv_sp_f[0]);
-        const float ty = floorf((y - P.org_f[1]) * P.inv_sp_f[1]);
+        const float tx = floorf(__fmul_rn(__fsub_rn(x, P.org_f[0]), P.inv_sp_f[0]));
+        const float ty = floorf(__fmul_rn(__fsub_rn(y, P.org_f[1]), P.inv_sp_f[1]));
         const bool inxy = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny;
         const int base = (int)tx + P.nx * (int)ty;
-        const float za = floorf((z - P.org_f[2]) * P.inv_sp_f[2]);
-        const float zb = floorf((z + h - P.org_f[2]) * P.inv_sp_f[2]);
-        const float zc = floorf((z - h - P.org_f[2]) * P.inv_sp_f[2]);
+        const float za = floorf(__fmul_rn(__fsub_rn(z, P.org_f[2]), P.inv_sp_f[2]));
+        const float zb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
+        const float zc = floorf(__fmul_rn(__fsub_rn(__fsub_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
         const int plane = P.nx * P.ny;
         ra = (inxy && za >= 0.f && za < (float)P.nz) ? __ldg(P.grid + base + plane * (int)za) : 0.0f;
         rb = (inxy && zb >= 0.f && zb < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zb) : 0.0f;

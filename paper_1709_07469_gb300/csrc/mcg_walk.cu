@@ -295,11 +295,13 @@ __device__ __forceinline__ double exit_mixed(const WalkParams& P, const float* X
 }
 
 // Exit records of the mixed walk (structure of arrays, item-major):
-//   frec[(8 c + f) * total + item], f = 0..2 X, 3..5 Y, 6 partial sum, 7 rho(X)
+//   frec[(8 c + f) * total + item], f = 0..2 walk position X before the exit
+//        step (copy 0's coordinates; copy c adds its z offset), 3..5 Y, 6 partial sum
 //   drec[c * total + item]          flushed double sum (NaN: no result)
+// rho at X is not stored: exit_mixed_kernel evaluates the same single-precision
+// density function at the same X, which gives the walk's value bit for bit.
 __device__ __forceinline__ void put_exit(const WalkParams& P, int c, unsigned long long item, float x0, float x1,
-                                         float x2, float y0, float y1, float y2, float partial, float rp,
-                                         double flushed)
+                                         float x2, float y0, float y1, float y2, float partial, double flushed)
 {
     float* f = P.frec + (size_t)8 * c * P.total + item;
     const size_t T = P.total;
@@ -310,7 +312,6 @@ __device__ __forceinline__ void put_exit(const WalkParams& P, int c, unsigned lo
     f[4 * T] = y1;
     f[5 * T] = y2;
     f[6 * T] = partial;
-    f[7 * T] = rp;
     P.drec[(size_t)c * T + item] = flushed;
 }
 
@@ -513,20 +514,22 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 template <int RHO, bool CRN, bool BRIDGE, bool BALL>
 __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
 {
+    // Per-walk state touched only at refills, exits and flushes lives in
+    // shared memory (one slot per thread); the step loop keeps the position,
+    // the partial sums, the path indices and the live-copy mask in registers.
+    __shared__ double sh_D[3][128];              // flushed sums per copy
+    __shared__ unsigned long long sh_item[128];  // work item of the walk
+    __shared__ long long sh_steps[128];          // EM steps of the copies that have exited
+    const int t = threadIdx.x;
     bool busy = false, exhausted = false;
-    unsigned long long item = 0ull;
     uint32_t s = 0u, p = 0u, blk = 0u;
     float wx = 0.f, wy = 0.f, wz = 0.f;
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;   // single-precision partial sums
-    double D0 = 0.0, D1 = 0.0, D2 = 0.0;  // flushed sums
-    float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // rho at the previous point
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;  // single-precision partial sums
     unsigned alive = 0u;
-    int64_t steps = 0;
-    bool zero_r = false;                  // r0..r2 are 0 (the last steps skipped the lookups)
     const float hx = P.half_f[0], hy = P.half_f[1], hz = P.half_f[2];
     const float hf = CRN ? P.h_f : 0.0f;
     unsigned round = 0u;
-    const int lane = threadIdx.x & 31;
+    const int lane = t & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
     const bool migrate = P.pool != nullptr;
     bool stop = false;     // cancelled: take no more work of any kind
@@ -539,21 +542,23 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             exhausted = true;
             stop = true;
         }
+        unsigned long long item = 0ull;
         if (refill(P, busy, exhausted, item) &&
             station_ok(P, s = (uint32_t)(item / (unsigned long long)P.N), item)) {
             p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
             wx = (float)(P.stations[3 * s + 0] - P.cen[0]);
             wy = (float)(P.stations[3 * s + 1] - P.cen[1]);
             wz = (float)(P.stations[3 * s + 2] - P.cen[2]);
+            float r0, r1, r2;
             rho3_f32<RHO>(P, wx, wy, wz, hf, r0, r1, r2);
             S0 = 0.5f * r0;
             S1 = 0.5f * r1;
             S2 = 0.5f * r2;
-            D0 = D1 = D2 = 0.0;
+            sh_D[0][t] = sh_D[1][t] = sh_D[2][t] = 0.0;
+            sh_item[t] = item;
+            sh_steps[t] = 0;
             alive = CRN ? 7u : 1u;
             blk = 0u;
-            steps = 0;
-            zero_r = false;
             busy = true;
         }
         if (migrate && !stop) {
@@ -576,23 +581,19 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     if (ready) {
                         const uint4* e = (const uint4*)(P.pool + slot * kPoolEntryBytes);
                         const uint4 e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3], e4 = e[4];
-                        item = ((unsigned long long)e0.y << 32) | e0.x;
-                        s = (uint32_t)(item / (unsigned long long)P.N);
-                        p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
+                        sh_item[t] = ((unsigned long long)e0.y << 32) | e0.x;
                         blk = e0.z;
                         alive = e0.w;
                         wx = __uint_as_float(e1.x);
                         wy = __uint_as_float(e1.y);
                         wz = __uint_as_float(e1.z);
-                        r0 = __uint_as_float(e1.w);
-                        r1 = __uint_as_float(e2.x);
-                        r2 = __uint_as_float(e2.y);
-                        steps = (int64_t)(((unsigned long long)e2.w << 32) | e2.z);
-                        D0 = __hiloint2double((int)e3.y, (int)e3.x);
-                        D1 = __hiloint2double((int)e3.w, (int)e3.z);
-                        D2 = __hiloint2double((int)e4.y, (int)e4.x);
+                        s = e1.w;
+                        p = e2.x;
+                        sh_steps[t] = (long long)(((unsigned long long)e2.w << 32) | e2.z);
+                        sh_D[0][t] = __hiloint2double((int)e3.y, (int)e3.x);
+                        sh_D[1][t] = __hiloint2double((int)e3.w, (int)e3.z);
+                        sh_D[2][t] = __hiloint2double((int)e4.y, (int)e4.x);
                         S0 = S1 = S2 = 0.f;
-                        zero_r = false;
                         busy = true;
                     } else {
                         atomicOr(P.status, 1 << MCG_ERR_TIMEOUT);
@@ -611,16 +612,14 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                 base = __shfl_sync(kFull, base, 0);
                 if (busy) {
                     const unsigned long long slot = base + (unsigned)__popc(livem & lanes_below);
-                    D0 += (double)S0;
-                    D1 += (double)S1;
-                    D2 += (double)S2;
-                    const float q0 = zero_r ? 0.f : r0, q1 = zero_r ? 0.f : r1, q2 = zero_r ? 0.f : r2;
+                    const unsigned long long it = sh_item[t];
+                    const unsigned long long st = (unsigned long long)sh_steps[t];
+                    const double D0 = sh_D[0][t] + (double)S0, D1 = sh_D[1][t] + (double)S1,
+                                 D2 = sh_D[2][t] + (double)S2;
                     uint4* e = (uint4*)(P.pool + slot * kPoolEntryBytes);
-                    e[0] = make_uint4((uint32_t)item, (uint32_t)(item >> 32), blk, alive);
-                    e[1] = make_uint4(__float_as_uint(wx), __float_as_uint(wy), __float_as_uint(wz),
-                                      __float_as_uint(q0));
-                    e[2] = make_uint4(__float_as_uint(q1), __float_as_uint(q2), (uint32_t)(unsigned long long)steps,
-                                      (uint32_t)((unsigned long long)steps >> 32));
+                    e[0] = make_uint4((uint32_t)it, (uint32_t)(it >> 32), blk, alive);
+                    e[1] = make_uint4(__float_as_uint(wx), __float_as_uint(wy), __float_as_uint(wz), s);
+                    e[2] = make_uint4(p, 0u, (uint32_t)st, (uint32_t)(st >> 32));
                     e[3] = make_uint4((uint32_t)__double2loint(D0), (uint32_t)__double2hiint(D0),
                                       (uint32_t)__double2loint(D1), (uint32_t)__double2hiint(D1));
                     e[4] = make_uint4((uint32_t)__double2loint(D2), (uint32_t)__double2hiint(D2), 0u, 0u);
@@ -663,13 +662,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     } else if constexpr (RHO == MCG_RHO_VOXEL) {
                         no_rho = false;
                     }
-                    if (inside_all && no_rho) {
-                        zero_r = true;  // rho = 0 at every copy: the partial sums do not change
-                    } else {
-                        if (zero_r) {
-                            r0 = r1 = r2 = 0.f;
-                            zero_r = false;
-                        }
+                    if (!(inside_all && no_rho)) {  // otherwise rho = 0 at every copy: sums unchanged
                         if (!inside_all) {
                             unsigned ins;
                             if (BALL) {
@@ -689,13 +682,11 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                             }
                             const unsigned out = alive & ~ins;
                             if (out) {  // some copy left Omega on this step
-                                const int64_t nstep = 4 * (int64_t)blk + m + 1;
-                                if (out & 1u) put_exit(P, 0, item, wx, wy, wz, nx, ny, nz, S0, r0, D0);
-                                if (CRN && (out & 2u))
-                                    put_exit(P, 1, item, wx, wy, wz + hf, nx, ny, nz + hf, S1, r1, D1);
-                                if (CRN && (out & 4u))
-                                    put_exit(P, 2, item, wx, wy, wz - hf, nx, ny, nz - hf, S2, r2, D2);
-                                steps += nstep * (int64_t)__popc(out);
+                                const unsigned long long it = sh_item[t];
+                                if (out & 1u) put_exit(P, 0, it, wx, wy, wz, nx, ny, nz, S0, sh_D[0][t]);
+                                if (CRN && (out & 2u)) put_exit(P, 1, it, wx, wy, wz, nx, ny, nz + hf, S1, sh_D[1][t]);
+                                if (CRN && (out & 4u)) put_exit(P, 2, it, wx, wy, wz, nx, ny, nz - hf, S2, sh_D[2][t]);
+                                sh_steps[t] += nstep_of(blk, m) * (long long)__popc(out);
                                 alive &= ins;
                             }
                             if (BRIDGE && alive) {  // within the bridge band of a face
@@ -703,6 +694,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                                 const unsigned bx = bridge_exits_f32(P, alive, wx, wy, wz, nx, ny, nz, hf, s, p, blk, m,
                                                                      &faces);
                                 if (bx) {
+                                    const unsigned long long it = sh_item[t];
                                     const float yb[3] = {nx, ny, nz};
                                     for (int c = 0; c < 3; ++c) {
                                         if (!(bx & (1u << c))) continue;
@@ -710,11 +702,10 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                                         float y3[3] = {yb[0], yb[1], yb[2] + off};
                                         const int f = (int)((faces >> (3 * c)) & 7u);
                                         y3[f >> 1] = (f & 1) ? P.half_f[f >> 1] : -P.half_f[f >> 1];
-                                        if (c == 0) put_exit(P, 0, item, wx, wy, wz, y3[0], y3[1], y3[2], S0, r0, D0);
-                                        if (c == 1) put_exit(P, 1, item, wx, wy, wz + hf, y3[0], y3[1], y3[2], S1, r1, D1);
-                                        if (c == 2) put_exit(P, 2, item, wx, wy, wz - hf, y3[0], y3[1], y3[2], S2, r2, D2);
+                                        const float part = c == 0 ? S0 : (c == 1 ? S1 : S2);
+                                        put_exit(P, c, it, wx, wy, wz, y3[0], y3[1], y3[2], part, sh_D[c][t]);
                                     }
-                                    steps += nstep_of(blk, m) * (int64_t)__popc(bx);
+                                    sh_steps[t] += nstep_of(blk, m) * (long long)__popc(bx);
                                     alive &= ~bx;
                                 }
                             }
@@ -722,12 +713,9 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         float ra, rb, rc;
                         rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
                         S0 += ra;
-                        r0 = ra;
                         if (CRN) {
                             S1 += rb;
                             S2 += rc;
-                            r1 = rb;
-                            r2 = rc;
                         }
                     }
                     wx = nx;
@@ -737,12 +725,13 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                 }
                 ++blk;
                 if (!alive) {
-                    P.pp_steps[item] = steps;
+                    P.pp_steps[sh_item[t]] = sh_steps[t];
                     busy = false;
                 } else if (4 * (int64_t)blk >= P.max_steps) {
+                    const unsigned long long it = sh_item[t];
                     atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
-                    P.drec[item] = kNaN;  // copy 0 record marks "no result"
-                    P.pp_steps[item] = steps + (int64_t)__popc(alive) * 4 * (int64_t)blk;
+                    P.drec[it] = kNaN;  // copy 0 record marks "no result"
+                    P.pp_steps[it] = sh_steps[t] + (long long)__popc(alive) * 4 * (long long)blk;
                     busy = false;
                 }
             }
@@ -750,19 +739,23 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             if (__popc(__ballot_sync(kFull, !busy && !exhausted)) >= P.refill_min) break;
         }
         // warp-uniform flush of the partial sums (at most 16 blocks = 64 steps each)
-        D0 += (double)S0;
+        sh_D[0][t] += (double)S0;
         S0 = 0.f;
         if (CRN) {
-            D1 += (double)S1;
-            D2 += (double)S2;
+            sh_D[1][t] += (double)S1;
+            sh_D[2][t] += (double)S2;
             S1 = S2 = 0.f;
         }
     }
 }
 
-// Per-path values from the exit records (convergent double precision).
+// Per-path values from the exit records (convergent double precision).  The
+// density at the last inside point is re-evaluated from X by the walk's own
+// single-precision function.
+template <int RHO>
 __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
 {
+    const float hf = P.crn ? P.h_f : 0.0f;
     for (unsigned long long item = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; item < P.total;
          item += (unsigned long long)gridDim.x * blockDim.x) {
         double u[3] = {kNaN, kNaN, kNaN};
@@ -772,8 +765,12 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
             for (int c = 0; c < nc; ++c) {
                 const float* f = P.frec + (size_t)8 * c * P.total + item;
                 const size_t T = P.total;
-                const float X[3] = {f[0], f[T], f[2 * T]}, Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
-                u[c] = exit_mixed(P, X, Y, P.drec[(size_t)c * T + item], f[6 * T], f[7 * T]);
+                const float xb = f[0], yb = f[T], zb = f[2 * T];
+                float r[3];
+                rho3_f32<RHO>(P, xb, yb, zb, hf, r[0], r[1], r[2]);
+                const float X[3] = {xb, yb, c == 0 ? zb : (c == 1 ? zb + hf : zb - hf)};
+                const float Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
+                u[c] = exit_mixed(P, X, Y, P.drec[(size_t)c * T + item], f[6 * T], r[c]);
             }
             const double d = P.crn ? (u[1] - u[2]) / (2.0 * P.h) : kNaN;
             P.pp_u[item] = u[0];
@@ -797,7 +794,7 @@ cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned long long need = (P.total + 127ull) / 128ull;
     const unsigned long long cap = (unsigned long long)sms * 16ull;
-    exit_mixed_kernel<<<(unsigned)(need < cap ? need : cap), 128, 0, st>>>(P);
+    exit_mixed_kernel<RHO><<<(unsigned)(need < cap ? need : cap), 128, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -858,7 +855,10 @@ void preload_walk_kernels()
 {
     touch(walk_fp64_kernel<true>);
     touch(walk_fp64_kernel<false>);
-    touch(exit_mixed_kernel);
+    touch(exit_mixed_kernel<MCG_RHO_NONE>);
+    touch(exit_mixed_kernel<MCG_RHO_SPHERE>);
+    touch(exit_mixed_kernel<MCG_RHO_PRISM>);
+    touch(exit_mixed_kernel<MCG_RHO_VOXEL>);
     touch_mixed<MCG_RHO_NONE>();
     touch_mixed<MCG_RHO_SPHERE>();
     touch_mixed<MCG_RHO_PRISM>();
