@@ -111,7 +111,7 @@ __device__ __forceinline__ bool cancelled(const WalkParams& P)
 // Each warp spills at most once, so slots are never reused.
 // ---------------------------------------------------------------------------
 #ifndef MCG_SPILL_MAX
-#define MCG_SPILL_MAX 8
+#define MCG_SPILL_MAX 24
 #endif
 #ifndef MCG_SPILL_BACKLOG
 #define MCG_SPILL_BACKLOG 64
