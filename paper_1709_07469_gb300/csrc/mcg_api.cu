@@ -470,8 +470,9 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
 
     int64_t batch = opts.batch_paths;
     if (batch <= 0) {
-        // per-path buffers and exit records of at most ~4 GiB per launch
-        const int64_t cap = (int64_t)((4ull << 30) / (152ull * (unsigned long long)S));
+        // per-path buffers, exit records and migration pool of at most ~4 GiB per launch
+        const double per_path = (double)mcg_workspace_bytes(S, 4096) / (4096.0 * (double)S);
+        const int64_t cap = (int64_t)((double)(4ull << 30) / (per_path * (double)S));
         batch = paths < cap ? paths : (cap > 0 ? cap : 1);
     }
     if (batch > paths) batch = paths;

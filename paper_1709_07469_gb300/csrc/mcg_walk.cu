@@ -749,38 +749,68 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
     }
 }
 
-// Per-path values from the exit records (convergent double precision).  The
+// Per-path values of one item from its exit records (double precision).  The
 // density at the last inside point is re-evaluated from X by the walk's own
 // single-precision function.
 template <int RHO>
+__device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long long item, float hf)
+{
+    double u[3] = {kNaN, kNaN, kNaN};
+    const int nc = P.crn ? 3 : 1;
+    const size_t T = P.total;
+    for (int c = 0; c < nc; ++c) {
+        const float* f = P.frec + (size_t)8 * c * T + item;
+        const float xb = f[0], yb = f[T], zb = f[2 * T];
+        float r[3];
+        rho3_f32<RHO>(P, xb, yb, zb, hf, r[0], r[1], r[2]);
+        const float X[3] = {xb, yb, c == 0 ? zb : (c == 1 ? zb + hf : zb - hf)};
+        const float Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
+        u[c] = exit_mixed(P, X, Y, P.drec[(size_t)c * T + item], f[6 * T], r[c]);
+    }
+    const double d = P.crn ? (u[1] - u[2]) / (2.0 * P.h) : kNaN;
+    P.pp_u[item] = u[0];
+    P.pp_d[item] = d;
+    if (!isfinite(u[0]) || (P.crn && !isfinite(d))) atomicOr(P.status, 1 << MCG_ERR_NONFINITE);
+}
+
+// Exit evaluation, convergent: each warp scans its items 32 at a time, writes
+// NaN for the ones without a result (capped, cancelled, outside Omega) and
+// queues the others in shared memory, evaluating them 32 at a time, so the
+// slow double-precision pipe never runs a warp whose lanes are mostly idle.
+template <int RHO>
 __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
 {
+    __shared__ unsigned long long queue[4][64];
     const float hf = P.crn ? P.h_f : 0.0f;
-    for (unsigned long long item = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; item < P.total;
-         item += (unsigned long long)gridDim.x * blockDim.x) {
-        double u[3] = {kNaN, kNaN, kNaN};
-        const int nc = P.crn ? 3 : 1;
-        const bool valid = !isnan(P.drec[item]);
-        if (valid) {
-            for (int c = 0; c < nc; ++c) {
-                const float* f = P.frec + (size_t)8 * c * P.total + item;
-                const size_t T = P.total;
-                const float xb = f[0], yb = f[T], zb = f[2 * T];
-                float r[3];
-                rho3_f32<RHO>(P, xb, yb, zb, hf, r[0], r[1], r[2]);
-                const float X[3] = {xb, yb, c == 0 ? zb : (c == 1 ? zb + hf : zb - hf)};
-                const float Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
-                u[c] = exit_mixed(P, X, Y, P.drec[(size_t)c * T + item], f[6 * T], r[c]);
-            }
-            const double d = P.crn ? (u[1] - u[2]) / (2.0 * P.h) : kNaN;
-            P.pp_u[item] = u[0];
-            P.pp_d[item] = d;
-            if (!isfinite(u[0]) || (P.crn && !isfinite(d))) atomicOr(P.status, 1 << MCG_ERR_NONFINITE);
-        } else {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long* q = queue[w];
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long first = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + w) * 32ull;
+    int qn = 0;  // queued items (warp-uniform)
+    for (unsigned long long base = first; base < P.total; base += warps * 32ull) {
+        const unsigned long long item = base + (unsigned long long)lane;
+        const bool in = item < P.total;
+        const bool valid = in && !isnan(P.drec[item]);
+        if (in && !valid) {
             P.pp_u[item] = kNaN;
             P.pp_d[item] = kNaN;
         }
+        const unsigned vm = __ballot_sync(kFull, valid);
+        if (valid) q[qn + __popc(vm & ((1u << lane) - 1u))] = item;
+        qn += __popc(vm);
+        __syncwarp();
+        if (qn >= 32) {
+            exit_item<RHO>(P, q[lane], hf);
+            const int rest = qn - 32;
+            unsigned long long v = 0ull;
+            if (lane < rest) v = q[32 + lane];
+            __syncwarp();
+            if (lane < rest) q[lane] = v;
+            __syncwarp();
+            qn = rest;
+        }
     }
+    if (lane < qn) exit_item<RHO>(P, q[lane], hf);
 }
 
 template <int RHO, bool CRN, bool BRIDGE, bool BALL>
