@@ -40,12 +40,19 @@ UNIT = "path-steps/s"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # Ideal lane-instruction count of the mixed walk per RNG-step (one Gaussian
-# triple advancing the three common-random-number copies), model in the design doc:
+# triple advancing the three common-random-number copies), counting the
+# minimal instruction for each operation the step needs:
 # Philox 30 + uniforms 6 + Box-Muller 12 + position 3 + exit test 7 +
 # density 13 + trapezoid 3 = 74; per path-step (3 copies) 74 / 3.
 OPS_PER_RNG_STEP = 74.0
 OPS_PER_PATH_STEP = OPS_PER_RNG_STEP / 3.0
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one walk_mixed_kernel launch per work item,
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum on 30 x 8192 items of
+# this workload (36.2-38.3 MB per launch over three launches);
+# traffic grows with the items, so a launch of n items moves ~150 n bytes.
+# To be re-measured (or reported as null) whenever the walk kernel changes.
+WALK_DRAM_BYTES_PER_ITEM = 150.0
 
 
 def parse():
@@ -54,7 +61,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=32768, help="paths per station per step")
+    ap.add_argument("--batch", type=int, default=131072,
+                    help="paths per station per step (131072: the 10^6 paths of the workload in ~8 steps)")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the walk (0: library default)")
     ap.add_argument("--migrate", type=int, default=1, choices=[0, 1],
                     help="hand the last walks of sparse warps to warps with free lanes (default 1)")
@@ -229,8 +237,9 @@ def run_ours(args):
     opts = [M.options(w, precision=M.MCG_MIXED, stream=s, block=args.block, migrate=args.migrate) for s in streams]
 
     def path_block(j):
-        # step j of this rank takes paths [p0, p0 + Bp) of every station (wrapping)
-        return ((j * world + rank) * Bp) % total_paths
+        # step j of this rank takes paths [p0, p0 + Bp) of every station: a
+        # fresh path range per step and rank (path indices stay below 2^31)
+        return ((j * world + rank) * Bp) % ((2**31 // Bp) * Bp)
 
     n_steps = args.warmup + args.steps
     ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)] for k in
@@ -317,7 +326,9 @@ def run_ours(args):
         achieved = per_launch_ops / per_launch_s / 1e12
         peak = SM_COUNT * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
-                           "frac": achieved / peak, "traffic": None,
+                           "frac": achieved / peak,
+                           "traffic": WALK_DRAM_BYTES_PER_ITEM * S * Bp,
+                           "traffic_source": "ncu dram bytes per item on 30 x 8192 items, scaled to the launch",
                            "kernel": "walk_mixed_kernel<PRISM,crn>",
                            "ops_per_rng_step": OPS_PER_RNG_STEP,
                            "launch_time": "timed region / K (two-stream pipeline)",
