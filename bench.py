@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="threads per block of the walk (0: library default)")
     ap.add_argument("--migrate", type=int, default=1, choices=[0, 1],
                     help="hand the last walks of sparse warps to warps with free lanes (default 1)")
-    ap.add_argument("--cpu-paths", type=int, default=48, help="paths per station in the CPU-oracle sample")
+    ap.add_argument("--cpu-paths", type=int, default=256, help="paths per station in the CPU-oracle sample")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="replay a Poisson trace of solve requests over 16 voxel models through the server")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serving trace")
-    ap.add_argument("--rate", type=float, default=200.0, help="mean arrival rate of the serving trace (1/s)")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="also replay the serving trace at this mean arrival rate (1/s)")
     ap.add_argument("--large-survey", action="store_true",
                     help="2e4 stations over the voxel model in one autotuned launch per step")
     ap.add_argument("--survey-paths", type=int, default=512, help="paths per station per large-survey step")
@@ -158,10 +159,10 @@ def barrier(world):
 
 # --- CPU oracle -----------------------------------------------------------------
 
-def cpu_oracle_rate(w, paths, p0=0):
+def cpu_oracle_rate(w, paths, p0=0, threads=None):
     import oracle
     from tests.helpers import oracle_spec
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     r = oracle.solve(oracle_spec(w, ubits=32), w.stations, paths, p0=p0, threads=threads)
     dt = time.perf_counter() - t0
@@ -341,9 +342,13 @@ def run_ours(args):
             out["e2e_blocking_solve"] = e2e_solve(M, w, Bp, max(1, min(args.steps, 3)))
         if not args.skip_cpu:
             rate, dt, cores, _ = cpu_oracle_rate(w, args.cpu_paths)
+            n1 = max(1, args.cpu_paths // 16)
+            rate1, dt1, _, _ = cpu_oracle_rate(w, n1, p0=args.cpu_paths, threads=1)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                    "sample": f"{S} stations x {args.cpu_paths} paths of prism_ore_body, "
-                                             f"FP64 oracle, {dt:.1f} s wall"}
+                                             f"FP64 oracle, {dt:.1f} s wall",
+                                   "single_core": {"value": rate1, "unit": UNIT,
+                                                   "sample": f"{S} stations x {n1} paths, 1 thread, {dt1:.1f} s"}}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 step / f64 accumulate", "data": "synthetic",
@@ -474,9 +479,12 @@ def e2e_server(M, w, Bp, steps):
 
 def run_serving(args):
     """Serving mix: 16 device-resident voxel models (GRF density, boundary
-    tables), Poisson arrivals, 1-64 stations per request, relative-SE targets
-    drawn from {1e-2, 3e-3, 1e-3}; requests are submitted at their arrival
-    times and complete as the server's rounds meet their targets."""
+    tables), 1-64 stations per request, relative-SE targets drawn from
+    {1e-2, 3e-3, 1e-3}.  First the capacity (all requests submitted at once,
+    requests/s = n / makespan), then Poisson replays of the same requests at
+    50 %, 80 % and 120 % of that capacity (and at --rate if given), each with
+    p50 / p99 latency (submit -> completion) and stations/s.  Requests complete
+    as the server's rounds meet their targets."""
     import torch
 
     from paper_1709_07469_gb300 import build as B
@@ -498,44 +506,58 @@ def run_serving(args):
     setup_s = time.perf_counter() - t0
     rng = np.random.default_rng(1234)
     n = args.requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n))
+    unit_gaps = rng.exponential(1.0, n)
     S = rng.integers(1, 65, n)
     targets = rng.choice([1e-2, 3e-3, 1e-3], n)
     mk = rng.integers(0, 16, n)
     st_idx = [rng.choice(base.n_stations, size=int(s), replace=False) for s in S]
-    cfg = M.server_config(M.options(base, precision=M.MCG_MIXED), chunk_paths=4096, min_paths=8192,
-                          hbm_budget=16 << 30, streams=8, max_active=64)
-    sv = M.mcg_server_create(cfg)
-    reqs = [None] * n
-    t_start = time.perf_counter()
-    i = 0
-    lat, path_steps, stations_done = [], 0, 0
-    outstanding = set()
-    while i < n or outstanding:
-        now = time.perf_counter() - t_start
-        while i < n and arrivals[i] <= now:
-            reqs[i] = M.mcg_submit(sv, models[mk[i]], base.stations[st_idx[i]], float(targets[i]), i)
-            outstanding.add(i)
-            i += 1
-        for j in list(outstanding):
-            done, rc, out = M.mcg_poll(reqs[j], int(S[j]))
-            if done:
-                assert rc == M.MCG_OK, (j, rc, M.last_error())
-                lat.append(M.mcg_request_info(reqs[j])[2] * 1e3)
-                path_steps += int(out["path_steps"].sum())
-                stations_done += int(S[j])
-                M.mcg_request_free(reqs[j])
-                outstanding.discard(j)
-        time.sleep(0.0005)
-    makespan = time.perf_counter() - t_start
-    M.mcg_server_destroy(sv)
+    cfg = M.server_config(M.options(base, precision=M.MCG_MIXED, migrate=args.migrate), chunk_paths=4096,
+                          min_paths=8192, hbm_budget=16 << 30, streams=8, max_active=64)
+
+    def replay(arrivals):
+        sv = M.mcg_server_create(cfg)
+        reqs = [None] * n
+        t_start = time.perf_counter()
+        i = 0
+        lat, path_steps, stations_done = [], 0, 0
+        outstanding = set()
+        while i < n or outstanding:
+            now = time.perf_counter() - t_start
+            while i < n and arrivals[i] <= now:
+                reqs[i] = M.mcg_submit(sv, models[mk[i]], base.stations[st_idx[i]], float(targets[i]), i)
+                outstanding.add(i)
+                i += 1
+            for j in list(outstanding):
+                done, rc, out = M.mcg_poll(reqs[j], int(S[j]))
+                if done:
+                    assert rc == M.MCG_OK, (j, rc, M.last_error())
+                    lat.append(M.mcg_request_info(reqs[j])[2] * 1e3)
+                    path_steps += int(out["path_steps"].sum())
+                    stations_done += int(S[j])
+                    M.mcg_request_free(reqs[j])
+                    outstanding.discard(j)
+            time.sleep(0.0005)
+        makespan = time.perf_counter() - t_start
+        M.mcg_server_destroy(sv)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "stations_per_s": stations_done / makespan, "path_steps_per_s": path_steps / makespan,
+                "makespan_s": makespan, "offered_span_s": float(arrivals[-1])}
+
+    closed = replay(np.zeros(n))
+    capacity = n / closed["makespan_s"]
+    levels = [("closed (all at t = 0)", None, closed)]
+    rates = [(f"{int(f * 100)} % of capacity", f * capacity) for f in (0.5, 0.8, 1.2)]
+    if args.rate:
+        rates.append(("fixed rate", args.rate))
+    for name, rate in rates:
+        r = replay(np.cumsum(unit_gaps / rate))
+        levels.append((name, rate, r))
     for m in models:
         M.mcg_model_destroy(m)
-    line = {"metric": "serving: p50/p99 ms and stations/s over a Poisson request trace", "impl": "ours",
-            "requests": n, "rate_per_s": args.rate, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "stations_per_s": stations_done / makespan,
-            "path_steps_per_s": path_steps / makespan, "makespan_s": makespan,
-            "offered_span_s": float(arrivals[-1]), "model_setup_s": setup_s,
+    line = {"metric": "serving: p50/p99 ms and stations/s over Poisson request traces", "impl": "ours",
+            "requests": n, "capacity_requests_per_s": capacity,
+            "levels": [dict(load=name, rate_per_s=rate, **r) for name, rate, r in levels],
+            "model_setup_s": setup_s,
             "config": {"workload": "voxel_survey x 16 models (seeds 0-15)", "stations_per_request": "U{1..64}",
                        "targets": [1e-2, 3e-3, 1e-3], "chunk_paths": 4096, "streams": 8, "hbm_budget_gib": 16},
             "data": "synthetic", "dtype": "f32 step / f64 accumulate"}

@@ -383,3 +383,33 @@ def test_migration_voxel_rounding_only():
     assert np.array_equal(a[2], b[2])
     np.testing.assert_allclose(a[0], b[0], rtol=0, atol=4e-6 * np.abs(b[0]).max())
     assert np.mean(a[0] == b[0]) > 0.2   # paths that never migrated are bit-identical
+
+
+def test_prism_full_size_launch_sampled_paths_mixed():
+    """The benchmark's launch: prism ore body, 30 stations x 131072 paths in one
+    mixed-precision launch (migration on), at a path range of a later step.
+    Sampled (station, path) pairs are walked one by one by the oracle under
+    the same indices and the 23-bit uniforms of the single-precision walk:
+    most exit steps agree exactly, and where they do u agrees to single-
+    precision rounding of ~1e5 steps."""
+    w = W.prism_ore_body()
+    N, p0 = 131072, 5 * 131072
+    ds = DeviceSolve(w, batch=N, precision=M.MCG_MIXED)
+    ds.reset()
+    ds.walk(p0)
+    u, d, steps = ds.per_path()
+    assert int(ds.status[0].item()) == 0
+    assert np.all(np.isfinite(u)) and np.all(steps > 0)
+    spec = oracle_spec(w, ubits=23)
+    rng = np.random.default_rng(3)
+    picks = [(0, 0), (29, N - 1), (14, N // 2)] + [(int(a), int(b)) for a, b in
+                                                 zip(rng.integers(0, 30, 37), rng.integers(0, N, 37))]
+    same, rel = [], []
+    for s, j in picks:
+        rc, uc, st, _ = oracle.walk_path(spec, w.stations[s], s, p0 + j)
+        assert rc == 0
+        same.append(st.sum() == steps[s, j])
+        if same[-1]:
+            rel.append(abs(u[s, j] - uc[0]) / abs(uc[0]))
+    assert np.mean(same) > 0.8
+    assert np.median(rel) < 1e-5
