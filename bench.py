@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="replay a Poisson trace of solve requests over 16 voxel models through the server")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serving trace")
+    ap.add_argument("--serve-streams", type=int, default=8, help="CUDA streams of the server")
+    ap.add_argument("--max-round-paths", type=int, default=65536, help="largest serving round (paths per station)")
     ap.add_argument("--rate", type=float, default=0.0,
                     help="also replay the serving trace at this mean arrival rate (1/s)")
     ap.add_argument("--large-survey", action="store_true",
@@ -512,7 +514,8 @@ def run_serving(args):
     mk = rng.integers(0, 16, n)
     st_idx = [rng.choice(base.n_stations, size=int(s), replace=False) for s in S]
     cfg = M.server_config(M.options(base, precision=M.MCG_MIXED, migrate=args.migrate), chunk_paths=4096,
-                          min_paths=8192, hbm_budget=16 << 30, streams=8, max_active=64)
+                          min_paths=8192, hbm_budget=16 << 30, streams=args.serve_streams, max_active=64,
+                          max_round_paths=args.max_round_paths)
 
     def replay(arrivals):
         sv = M.mcg_server_create(cfg)
@@ -559,7 +562,8 @@ def run_serving(args):
             "levels": [dict(load=name, rate_per_s=rate, **r) for name, rate, r in levels],
             "model_setup_s": setup_s,
             "config": {"workload": "voxel_survey x 16 models (seeds 0-15)", "stations_per_request": "U{1..64}",
-                       "targets": [1e-2, 3e-3, 1e-3], "chunk_paths": 4096, "streams": 8, "hbm_budget_gib": 16},
+                       "targets": [1e-2, 3e-3, 1e-3], "chunk_paths": 4096, "streams": args.serve_streams,
+                       "max_round_paths": args.max_round_paths, "hbm_budget_gib": 16},
             "data": "synthetic", "dtype": "f32 step / f64 accumulate"}
     print(json.dumps(line), flush=True)
     return 0

@@ -326,13 +326,14 @@ MCG_API int mcg_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int6
  * station sets, models and accuracy targets (the paper's motivation, Sec. 1).
  * The server keeps models resident on the device, admits requests while
  * their buffers fit an HBM budget, and advances every admitted request in
- * rounds: one round walks `chunk_paths` more paths (path indices k*chunk ..
- * (k+1)*chunk - 1 of each station for round k) and merges them into the
- * request's station statistics; after each round the request stops once
- * every station reaches its relative standard error target (and has at
- * least min_paths paths) or max_paths.  Past min_paths a round walks as many
- * chunks (up to max_round_paths) as the request's own per-path spread says
- * it still needs, in one launch.  Rounds of different requests run on
+ * rounds of whole chunks of `chunk_paths` paths per station (path indices
+ * continue from round to round: the request's paths are 0, 1, 2, ... of
+ * each station), each merged into the request's station statistics; after
+ * each round the request stops once every station reaches its relative
+ * standard error target (and has at least min_paths paths) or max_paths.
+ * The first round walks min_paths (rounded up to chunks); later rounds walk
+ * as many chunks (up to max_round_paths) as the request's own per-path
+ * spread says it still needs, in one launch.  Rounds of different requests run on
  * a pool of streams and overlap on the GPU; a request's result depends only
  * on its own (seed, stations, target), never on what else is in flight.
  * All calls are thread-safe.  Objects are owned by the library until the

@@ -2,9 +2,9 @@
 //
 // A scheduler thread admits queued requests while their device buffers fit
 // the HBM budget, and advances every admitted request round by round on a
-// pool of CUDA streams: each round walks `chunk_paths` more paths of each of
-// the request's stations (round k takes path indices k*chunk ..
-// (k+1)*chunk-1), reduces them into the request's station statistics,
+// pool of CUDA streams: each round walks whole chunks of `chunk_paths` more
+// paths of each of the request's stations (path indices continue where the
+// last round stopped), reduces them into the request's station statistics,
 // finalizes and copies u, g_z, standard errors and path counts into pinned
 // host memory.  When a round's event has completed the thread decides on
 // the host whether the request reached its target; if not, it launches the
@@ -128,15 +128,20 @@ void finish(mcg_request* r, int status, const char* msg)
     r->cv.notify_all();
 }
 
-// Paths per station of the request's next round: one chunk until min_paths,
-// then the chunks the request's own spread says it still needs (90 % of the
-// estimate, at least one chunk, at most max_round_paths), never past
-// max_paths.  Depends only on the request's own results.
+// Paths per station of the request's next round: min_paths (in whole
+// chunks) first, then the chunks the request's own spread says it still needs
+// (90 % of the estimate, at least one chunk, at most max_round_paths), never
+// past max_paths.  Depends only on the request's own results.
 int64_t next_round_paths(const mcg_server* sv, const mcg_request* r)
 {
     const int64_t chunk = sv->cfg.chunk_paths;
     int64_t m = 1;
-    if (r->done_paths >= sv->cfg.min_paths) {
+    if (r->done_paths < sv->cfg.min_paths) {
+        // the first round takes the request straight to min_paths
+        m = (sv->cfg.min_paths - r->done_paths + chunk - 1) / chunk;
+        const int64_t mmax = sv->cfg.max_round_paths / chunk;
+        if (m > mmax) m = mmax;
+    } else {
         double need = 0.0;
         for (int64_t s = 0; s < r->S; ++s) {
             const double u = r->h_res[s], se = r->h_res[2 * r->S + s];
