@@ -27,7 +27,7 @@ namespace mcg {
 namespace {
 
 #ifndef MCG_MIXED_MINB
-#define MCG_MIXED_MINB 4
+#define MCG_MIXED_MINB 5
 #endif
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             continue;  // the last warp: take over the pooled walks
         }
 
-#pragma unroll 1
+#pragma unroll 2
         for (int k = 0; k < 16; ++k) {
             if (busy) {
                 float z[12];
