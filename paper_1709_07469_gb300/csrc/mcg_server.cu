@@ -16,6 +16,8 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -28,6 +30,53 @@
 
 using namespace mcg;
 using Clock = std::chrono::steady_clock;
+
+namespace {
+
+// Pinned host blocks reused across requests.  Allocating or freeing pinned
+// memory is not stream-ordered (and a pageable host->device copy waits for
+// its stream to drain), so a request never does either while others run:
+// its host side (station staging, results, status word) comes from this
+// pool, which grows on demand and frees its blocks when the last owner (the
+// server or a request still held by the caller) lets go of it.
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, void*> free_blocks;  // capacity -> block
+    std::vector<void*> all;
+    ~PinnedPool()
+    {
+        for (void* b : all) cudaFreeHost(b);
+    }
+    // A block of at least `bytes`; its capacity in *cap.  nullptr on failure.
+    void* take(size_t bytes, size_t* cap)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = free_blocks.lower_bound(bytes);
+        if (it != free_blocks.end() && it->first <= 4 * bytes + 4096) {
+            void* b = it->second;
+            *cap = it->first;
+            free_blocks.erase(it);
+            return b;
+        }
+        size_t c = 4096;
+        while (c < bytes) c *= 2;
+        void* b = nullptr;
+        if (cudaMallocHost(&b, c) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        all.push_back(b);
+        *cap = c;
+        return b;
+    }
+    void give(void* b, size_t cap)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free_blocks.emplace(cap, b);
+    }
+};
+
+}  // namespace
 
 struct mcg_model {
     mcg_domain dom;
@@ -42,7 +91,6 @@ struct mcg_model {
 struct mcg_request {
     mcg_server* server = nullptr;
     const mcg_model* model = nullptr;
-    std::vector<double> stations;
     int64_t S = 0;
     double target = 0.0;
     uint64_t seed = 0;
@@ -56,7 +104,9 @@ struct mcg_request {
     int64_t round_paths = 0;  // paths per station of the round in flight
     bool in_flight = false;
     cudaEvent_t ev = nullptr;
-    double* h_res = nullptr;  // pinned: 6 S doubles + status word
+    double* h_res = nullptr;  // pinned: 6 S doubles + status word + 3 S station coordinates
+    size_t h_cap = 0;         // capacity of the pinned block behind h_res
+    std::shared_ptr<PinnedPool> pinned;
     // published state
     std::mutex mu;
     std::condition_variable cv;
@@ -81,6 +131,8 @@ struct mcg_server {
     bool stopping = false;
     std::vector<mcg_request*> active;
     size_t used = 0;
+    std::shared_ptr<PinnedPool> pinned = std::make_shared<PinnedPool>();
+    cudaMemPool_t pool = nullptr;  // the server's own stream-ordered device pool
     std::thread th;
 };
 
@@ -202,15 +254,17 @@ int admit(mcg_server* sv, mcg_request* r)
     r->stream = best;
     cudaStream_t st = sv->streams[best];
     const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
-    cudaError_t e = cudaMallocAsync((void**)&r->dev, L.total, st);
+    cudaError_t e = cudaMallocFromPoolAsync((void**)&r->dev, L.total, sv->pool, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         r->dev = nullptr;
         return MCG_ERR_OOM;
     }
     r->bytes = L.total;
-    if ((e = cudaMemcpyAsync(r->dev + L.st, r->stations.data(), r->S * 3 * sizeof(double), cudaMemcpyHostToDevice,
-                             st)) ||
+    // from the pinned staging copy: a pageable source would make this call
+    // wait until the stream has drained
+    if ((e = cudaMemcpyAsync(r->dev + L.st, r->h_res + 6 * r->S + 1, r->S * 3 * sizeof(double),
+                             cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemsetAsync(r->dev + L.states, 0, r->S * sizeof(mcg_station_state), st)) ||
         (e = cudaMemsetAsync(r->dev + L.status, 0, 256, st))) {
         cudaFreeAsync(r->dev, st);
@@ -433,18 +487,36 @@ int mcg_server_create(const mcg_server_config* cfg_in, mcg_server** out)
     mcg_server* sv = new mcg_server();
     sv->cfg = cfg;
     cudaGetDevice(&sv->device);
-    // keep freed request buffers in the stream-ordered pool (up to the
-    // budget) instead of returning them to the driver after every request
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) {
+    // Request buffers come from a device pool of the server's own: freed
+    // buffers stay cached (up to the budget) instead of going back to the
+    // driver after every request, and a buffer freed on one stream is reused
+    // on another only once that free has completed -- the pool never makes
+    // one stream wait for another (no internal dependencies).  The process's
+    // default pool is left as it was.
+    {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = sv->device;
+        const cudaError_t e = cudaMemPoolCreate(&sv->pool, &props);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete sv;
+            return set_error(MCG_ERR_CUDA, "cudaMemPoolCreate: %s", cudaGetErrorString(e));
+        }
         uint64_t thr = (uint64_t)cfg.hbm_budget;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        int off = 0;
+        cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowInternalDependencies, &off);
     }
     for (int i = 0; i < cfg.streams; ++i) {
         cudaStream_t st;
         const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             for (cudaStream_t s2 : sv->streams) cudaStreamDestroy(s2);
+            cudaMemPoolDestroy(sv->pool);
             delete sv;
             return set_error(MCG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
         }
@@ -469,6 +541,7 @@ int mcg_server_destroy(mcg_server* sv)
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    cudaMemPoolDestroy(sv->pool);
     delete sv;
     return MCG_OK;
 }
@@ -492,23 +565,28 @@ int mcg_submit(mcg_server* sv, const mcg_model* m, const double* stations, int64
     }
     r->server = sv;
     r->model = m;
-    r->stations.assign(stations, stations + 3 * S);
     r->S = S;
     r->target = target_rel_se;
     r->seed = seed;
     cudaError_t e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_res, (6 * S + 1) * sizeof(double));
+    const size_t hbytes = (9 * (size_t)S + 1) * sizeof(double);
+    if (e == cudaSuccess) {
+        r->pinned = sv->pinned;
+        r->h_res = (double*)r->pinned->take(hbytes, &r->h_cap);
+        if (!r->h_res) e = cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
         if (r->ev) cudaEventDestroy(r->ev);
         delete r;
         return set_error(MCG_ERR_CUDA, "request set-up: %s", cudaGetErrorString(e));
     }
     std::memset(r->h_res, 0, (6 * S + 1) * sizeof(double));
+    std::memcpy(r->h_res + 6 * S + 1, stations, 3 * (size_t)S * sizeof(double));
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stopping) {
-            cudaFreeHost(r->h_res);
+            r->pinned->give(r->h_res, r->h_cap);
             cudaEventDestroy(r->ev);
             delete r;
             return set_error(MCG_ERR_ARG, "server is stopping");
@@ -586,7 +664,7 @@ int mcg_request_free(mcg_request* r)
         std::unique_lock<std::mutex> lk(r->mu);
         if (!r->done) return set_error(MCG_ERR_ARG, "request still running (cancel and wait first)");
     }
-    if (r->h_res) cudaFreeHost(r->h_res);
+    if (r->h_res) r->pinned->give(r->h_res, r->h_cap);
     if (r->ev) cudaEventDestroy(r->ev);
     delete r;
     return MCG_OK;
