@@ -22,7 +22,10 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
     o.refill_min = 1;
     int rc = make_params(domain, density, boundary, dt, seed, &o, P);
     if (rc) return rc;
-    const int64_t N = 2048;
+    // about 2.6e5 timed walks in all (a few per lane of the persistent grid),
+    // at most 2048 per station: enough to fill the GPU without a large scratch
+    int64_t N = (262144 + S - 1) / S;
+    if (N > 2048) N = 2048;
     const size_t n = (size_t)S * (size_t)N;
     const size_t work = mcg_walk_work_bytes(S, N, o.precision);
     const size_t bytes = 3 * align256(n * sizeof(double)) + align256(work) + 256;

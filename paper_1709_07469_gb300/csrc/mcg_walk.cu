@@ -643,9 +643,30 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             if (busy) {
                 float z[12];
                 normals12_f32(s, p, blk, P.key0, P.key1, P.lnscale_f, z);
+                // Voxel grid: the block's four positions are known once its
+                // normals are, so all twelve density loads are issued here
+                // and their latency overlaps the steps (same positions, same
+                // summation order: results are unchanged).
+                constexpr bool kPrefetch = RHO == MCG_RHO_VOXEL;
+                float px[4], py[4], pz[4], rv[4][3];
+                if constexpr (kPrefetch) {
+                    float x = wx, y = wy, zz = wz;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        x = x + z[3 * m];
+                        y = y + z[3 * m + 1];
+                        zz = zz + z[3 * m + 2];
+                        px[m] = x;
+                        py[m] = y;
+                        pz[m] = zz;
+                        rho3_f32<RHO>(P, x, y, zz, hf, rv[m][0], rv[m][1], rv[m][2]);
+                    }
+                }
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const float nx = wx + z[3 * m], ny = wy + z[3 * m + 1], nz = wz + z[3 * m + 2];
+                    const float nx = kPrefetch ? px[m] : wx + z[3 * m];
+                    const float ny = kPrefetch ? py[m] : wy + z[3 * m + 1];
+                    const float nz = kPrefetch ? pz[m] : wz + z[3 * m + 2];
                     // common step: every copy surely inside Omega and surely
                     // outside the density's support -> nothing to do but move
                     const float qxy = BALL ? nx * nx + ny * ny : 0.0f;
@@ -711,7 +732,13 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                             }
                         }
                         float ra, rb, rc;
-                        rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
+                        if constexpr (kPrefetch) {
+                            ra = rv[m][0];
+                            rb = rv[m][1];
+                            rc = rv[m][2];
+                        } else {
+                            rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
+                        }
                         S0 += ra;
                         if (CRN) {
                             S1 += rb;
