@@ -191,8 +191,12 @@ MCG_API const char* mcg_version(void);
  *   stations : HOST, S x 3 row-major (x, y, z).
  *   density, boundary : grid / faces are DEVICE pointers when used.
  *   out      : HOST arrays of length S.
- * Blocking.  Allocates a device workspace of mcg_workspace_bytes(S,
- * batch) for the duration of the call.  Returns MCG_ERR_STEP_CAP /
+ * Blocking.  Allocates a device workspace of at most mcg_workspace_bytes(S,
+ * batch) for the duration of the call.  With several batches, consecutive
+ * batches alternate between two streams (the caller's and one of the
+ * call's own) so that one batch's exit-time tail runs beside the next
+ * batch; the reductions stay in batch order, so the result does not depend
+ * on it.  Returns MCG_ERR_STEP_CAP /
  * MCG_ERR_NONFINITE when some path hit the cap / was not finite (the
  * statistics then include NaN). */
 MCG_API int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
@@ -299,8 +303,9 @@ MCG_API int mcg_autotune(const mcg_domain* domain, const mcg_density* density, c
  * not alias y.  Allocates nothing. */
 MCG_API int mcg_smooth_moving_average(const double* y, int64_t n, int32_t span, double* out);
 
-/* Bytes of device workspace mcgrav_solve uses for S stations and batches of
- * `batch` paths per station. */
+/* Bytes of device workspace mcgrav_solve uses at most for S stations and
+ * batches of `batch` paths per station (two sets of per-batch buffers; a
+ * solve of one batch uses one). */
 MCG_API size_t mcg_workspace_bytes(int64_t S, int64_t batch);
 
 /* ---------------------------------------------------------------------- */

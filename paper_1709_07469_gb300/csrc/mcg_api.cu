@@ -41,6 +41,24 @@ int set_error(int code, const char* fmt, ...)
 
 // Checks the problem description and fills the launch parameters (without
 // the work list, which the caller adds).
+// mcgrav_solve's workspace: a shared part (stations, station states, status
+// word, finalized results) and one or two per-launch sets (per-path values,
+// work counter, walk scratch) -- two when the solve has several batches, so
+// consecutive batches alternate between them on two streams.
+size_t solve_shared_bytes(int64_t S)
+{
+    const size_t s = (size_t)S;
+    return align256(s * 3 * sizeof(double)) + align256(s * sizeof(mcg_station_state)) + 256 +
+           align256(s * 6 * sizeof(double));
+}
+
+size_t solve_set_bytes(int64_t S, int64_t batch)
+{
+    const size_t n = (size_t)S * (size_t)batch;
+    return 2 * align256(n * sizeof(double)) + align256(n * sizeof(int64_t)) + 256 +
+           mcg_walk_work_bytes(S, batch, MCG_MIXED);
+}
+
 void preload_kernels()
 {
     static std::atomic<unsigned long long> loaded{0};  // one bit per device ordinal < 64
@@ -379,10 +397,7 @@ const char* mcg_version(void) { return "mcgrav 0.1 sm_103a"; }
 size_t mcg_workspace_bytes(int64_t S, int64_t batch)
 {
     if (S <= 0 || batch <= 0) return 0;
-    const size_t s = (size_t)S, n = (size_t)S * (size_t)batch;
-    return align256(s * 3 * sizeof(double)) + align256(s * sizeof(mcg_station_state)) + 256 /* status+counter */ +
-           align256(s * 6 * sizeof(double)) + 2 * align256(n * sizeof(double)) + align256(n * sizeof(int64_t)) +
-           mcg_walk_work_bytes(S, batch, MCG_MIXED);
+    return solve_shared_bytes(S) + 2 * solve_set_bytes(S, batch);
 }
 
 size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision)
@@ -476,7 +491,10 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
         batch = paths < cap ? paths : (cap > 0 ? cap : 1);
     }
     if (batch > paths) batch = paths;
-    const size_t bytes = mcg_workspace_bytes(S, batch);
+    const int64_t nbatch = (paths + batch - 1) / batch;
+    const int nsets = nbatch >= 2 ? 2 : 1;
+    const size_t set_bytes = solve_set_bytes(S, batch);
+    const size_t bytes = solve_shared_bytes(S) + (size_t)nsets * set_bytes;
     char* ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, bytes);
     if (e != cudaSuccess) {
@@ -491,17 +509,28 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     mcg_station_state* d_state = (mcg_station_state*)q;
     q += align256(s_ * sizeof(mcg_station_state));
     int32_t* d_status = (int32_t*)q;
-    unsigned long long* d_counter = (unsigned long long*)(q + 128);
     q += 256;
     double* d_res = (double*)q;
     q += align256(s_ * 6 * sizeof(double));
-    double* d_u = (double*)q;
-    q += align256(n_ * sizeof(double));
-    double* d_d = (double*)q;
-    q += align256(n_ * sizeof(double));
-    int64_t* d_steps = (int64_t*)q;
-    q += align256(n_ * sizeof(int64_t));
-    void* d_work = (void*)q;
+    struct BatchSet {
+        double* u;
+        double* d;
+        int64_t* steps;
+        unsigned long long* counter;
+        void* work;
+    } set[2] = {};
+    for (int k = 0; k < nsets; ++k) {
+        set[k].u = (double*)q;
+        q += align256(n_ * sizeof(double));
+        set[k].d = (double*)q;
+        q += align256(n_ * sizeof(double));
+        set[k].steps = (int64_t*)q;
+        q += align256(n_ * sizeof(int64_t));
+        set[k].counter = (unsigned long long*)q;
+        q += 256;
+        set[k].work = (void*)q;
+        q += mcg_walk_work_bytes(S, batch, MCG_MIXED);
+    }
 
     double* h_res = new double[6 * s_];
     int32_t h_status = 0;
@@ -513,31 +542,52 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
             rc = cuda_fail(e, "workspace initialisation");
             break;
         }
-        // The batches (counter reset, walk, exit evaluation, reduction) and
-        // the finalize, in order on one stream.  With several batches and
-        // opts.graph the sequence is captured once into a CUDA graph and
-        // launched as one unit.
-        const bool use_graph = opts.graph && paths > batch;
-        cudaStream_t run = st;
-        if (use_graph) {
-            if ((e = cudaStreamCreateWithFlags(&run, cudaStreamNonBlocking)) ||
-                (e = cudaStreamBeginCapture(run, cudaStreamCaptureModeThreadLocal))) {
-                rc = cuda_fail(e, "graph capture");
-                break;
-            }
+        // The batches (counter and pool reset, walk, exit evaluation,
+        // reduction), then the finalize.  With several batches, batch j runs
+        // on stream j % 2 with buffer set j % 2, so one batch's exit-time
+        // tail overlaps the next batch; each reduction waits for the one
+        // before it, so the statistics merge in batch order.  With opts.graph
+        // the whole sequence is captured once into a CUDA graph and launched
+        // as one unit.
+        const bool use_graph = opts.graph && nbatch >= 2;
+        cudaStream_t run = st, run2 = nullptr;
+        cudaEvent_t ev_fork = nullptr, ev_red = nullptr, ev_join = nullptr;
+        if ((use_graph && (e = cudaStreamCreateWithFlags(&run, cudaStreamNonBlocking))) ||
+            (nsets == 2 && (e = cudaStreamCreateWithFlags(&run2, cudaStreamNonBlocking))) ||
+            (e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&ev_red, cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) ||
+            (use_graph && (e = cudaStreamBeginCapture(run, cudaStreamCaptureModeThreadLocal)))) {
+            rc = cuda_fail(e, "stream / event / capture set-up");
         }
+        const bool capturing = use_graph && rc == MCG_OK;
+        if (rc == MCG_OK && nsets == 2) {
+            if ((e = cudaEventRecord(ev_fork, run)) || (e = cudaStreamWaitEvent(run2, ev_fork, 0)))
+                rc = cuda_fail(e, "stream fork");
+        }
+        cudaStream_t qs[2] = {run, run2};
         mcg_options ro = opts;
-        ro.stream = run;
-        for (int64_t p0 = 0; p0 < paths && rc == MCG_OK; p0 += batch) {
+        int64_t j = 0;
+        for (int64_t p0 = 0; p0 < paths && rc == MCG_OK; p0 += batch, ++j) {
             const int64_t nb = (paths - p0) < batch ? (paths - p0) : batch;
-            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &ro, d_u, d_d, d_steps, d_work,
-                          d_status, d_counter);
-            if (rc == MCG_OK) rc = mcg_reduce(d_u, d_d, d_steps, S, nb, d_state, run);
+            const int k = (int)(j % nsets);
+            ro.stream = qs[k];
+            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &ro, set[k].u, set[k].d,
+                          set[k].steps, set[k].work, d_status, set[k].counter);
+            if (rc == MCG_OK && j > 0 && (e = cudaStreamWaitEvent(qs[k], ev_red, 0)))
+                rc = cuda_fail(e, "reduction order");
+            if (rc == MCG_OK) rc = mcg_reduce(set[k].u, set[k].d, set[k].steps, S, nb, d_state, qs[k]);
+            if (rc == MCG_OK && (e = cudaEventRecord(ev_red, qs[k]))) rc = cuda_fail(e, "reduction order");
+        }
+        if (nsets == 2 && (capturing || rc == MCG_OK)) {
+            // join the second stream back (also required to end a capture)
+            if ((e = cudaEventRecord(ev_join, run2)) || (e = cudaStreamWaitEvent(run, ev_join, 0)))
+                if (rc == MCG_OK) rc = cuda_fail(e, "stream join");
         }
         if (rc == MCG_OK)
             rc = mcg_finalize(d_state, S, d_res, d_res + s_, d_res + 2 * s_, d_res + 3 * s_,
                               (int64_t*)(d_res + 4 * s_), (int64_t*)(d_res + 5 * s_), run);
-        if (use_graph) {
+        if (capturing) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             cudaError_t ge = cudaStreamEndCapture(run, &graph);
@@ -557,10 +607,21 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
             }
             if (exec) cudaGraphExecDestroy(exec);
             if (graph) cudaGraphDestroy(graph);
-            cudaStreamSynchronize(run);
-            cudaStreamDestroy(run);
             if (rc == MCG_OK && ge != cudaSuccess) rc = cuda_fail(ge, "graph launch");
         }
+        // the call's own streams and events: their work is waited for below
+        // (the result copy on st follows the join / the graph launch)
+        if (use_graph && run != st) {
+            cudaStreamSynchronize(run);
+            cudaStreamDestroy(run);
+        }
+        if (run2) {
+            cudaStreamSynchronize(run2);
+            cudaStreamDestroy(run2);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_red) cudaEventDestroy(ev_red);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (rc) break;
         if ((e = cudaMemcpyAsync(h_res, d_res, 6 * s_ * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
             (e = cudaMemcpyAsync(&h_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||

@@ -81,6 +81,9 @@ struct WorkLayout {
 WorkLayout work_layout(size_t n);
 // Points P's mixed-walk buffers into `work` (layout above); migration on/off.
 void bind_work(WalkParams& P, void* work, bool migrate);
+// mcgrav_solve's workspace parts (mcg_api.cu).
+size_t solve_shared_bytes(int64_t S);
+size_t solve_set_bytes(int64_t S, int64_t batch);
 // Zeroes the work counter and, with migration, the pool's flags and counters.
 cudaError_t reset_walk(const WalkParams& P, cudaStream_t st);
 

@@ -67,9 +67,9 @@ def test_defaults_and_workspace(lib):
     assert o.graph == 1 and o.refill_min == 1 and o.bridge == 0 and o.migrate == 1
     assert M.mcg_workspace_bytes(0, 10) == 0
     b = M.mcg_workspace_bytes(30, 1000)
-    # per path: u, d, steps (24 B) + the mixed walk's exit records (3 x 40 B)
-    # + a migration-pool slot (80 B) and its ready flag (4 B)
-    assert b >= 30 * 1000 * 228 and b < 30 * 1000 * 228 + 64 * 1024
+    # two per-batch sets; per path: u, d, steps (24 B) + the mixed walk's exit
+    # records (3 x 40 B) + a migration-pool slot (80 B) and its ready flag (4 B)
+    assert b >= 2 * 30 * 1000 * 228 and b < 2 * 30 * 1000 * 228 + 64 * 1024
     assert M.mcg_walk_work_bytes(30, 1000, M.MCG_FP64) == 0
     assert M.mcg_walk_work_bytes(30, 1000, M.MCG_MIXED) >= 30 * 1000 * 204
     # the pool stops growing at 2^19 slots

@@ -325,14 +325,21 @@ def test_paper_experiment_1_line():
 
 
 def test_mcgrav_solve_graph_equals_stream_launches():
-    """Several batches captured into one CUDA graph give the same numbers as
-    the same launches issued on the stream."""
-    w = W.sphere_line(paths=6000)
+    """Several batches (the last one ragged) alternate between two streams
+    inside mcgrav_solve; captured into one CUDA graph or issued directly,
+    they give the same numbers as the same batches run one after another on
+    one stream through the device-level entry points (same per-path values,
+    reductions in batch order)."""
+    w = W.sphere_line(paths=6500)
     prob = M.problem(w)
     a = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=1000, graph=1))
     b = M.mcgrav_solve(prob, w.stations, w.paths, w.dt, w.seed, M.options(w, batch_paths=1000, graph=0))
+    ds = DeviceSolve(w, batch=1000, precision=M.MCG_MIXED)
+    c = ds.run()
     for k in ("u", "gz", "se_u", "se_gz", "n_paths", "path_steps"):
         assert np.array_equal(getattr(a, k), getattr(b, k)), k
+        assert np.array_equal(getattr(a, k), c[k]), k
+    assert np.all(a.n_paths == 6500)
 
 
 def _per_path_migrate(w, migrate, **kw):
