@@ -320,7 +320,7 @@ def test_paper_experiment_1_line():
     off = W.G_SI * Mass / 10_000.0
     phi = np.array([oracle.prism_phi(W.G_SI, 2000.0, (0, 0, 0), (100, 100, 100), x) for x in w.stations])
     rel_offset = off / np.abs(phi)
-    assert np.all((rel_offset > 0.008) & (rel_offset < 0.03))     # the paper's "around 1 %"
+    assert np.all((rel_offset > 0.008) & (rel_offset < 0.03))     # the paper's offset of about 1 %
     assert np.all(np.abs(r["u"] - (phi + off)) < 4 * r["se_u"] + 0.01 * np.abs(phi))
 
 
