@@ -748,7 +748,9 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     wx = nx;
                     wy = ny;
                     wz = nz;
-                    if (!alive) break;
+                    // no early exit when the last copy leaves: the remaining
+                    // steps of the block write nothing (no live copy), and a
+                    // branch-free four-step body schedules better
                 }
                 ++blk;
                 if (!alive) {
