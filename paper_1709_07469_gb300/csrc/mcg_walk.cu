@@ -16,7 +16,12 @@
 //    and density lookup; the source integral keeps single-precision partial
 //    sums over at most 64 steps which are flushed into a double accumulator;
 //    the exit-segment clip, the boundary value and the per-path estimate are
-//    double precision.
+//    double precision and run in exit_mixed_kernel.  Once the work list is
+//    used up, walks migrate from sparse warps to warps with free lanes.
+//
+// Launch shape: 128 threads, at least MCG_MIXED_MINB blocks per SM (the
+// register bound that gave the best rate; the grid is sized from the
+// occupancy the compiled kernel actually gets).
 #include <cuda_runtime.h>
 
 #include "mcg_device.cuh"
@@ -506,10 +511,10 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 // arithmetic in the step loop.  The three common-random-number copies are
 // updated branch-free; exits (rare) take a side branch that writes an exit
 // record, which exit_mixed_kernel turns into per-path values.  A warp runs up
-// to 16 blocks (64 steps) between refills; after them it flushes the
-// single-precision partial sums into the double sums (a real, warp-uniform
-// branch, so the slow double-precision unit sees one instruction per copy per
-// 64 steps).
+// to 16 blocks (64 steps) between refills, two blocks per loop iteration;
+// after them it flushes the single-precision partial sums into the double
+// sums (a real, warp-uniform branch, so the slow double-precision unit sees
+// one instruction per copy per 64 steps).
 // ---------------------------------------------------------------------------
 template <int RHO, bool CRN, bool BRIDGE, bool BALL>
 __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
