@@ -85,7 +85,8 @@ typedef enum { MCG_RHO_NONE = 0, MCG_RHO_SPHERE = 1, MCG_RHO_PRISM = 2, MCG_RHO_
  * like the paper's cube model (Sec. 3).
  *   SPHERE: rho0 where |x - center| < radius (strict), else 0.
  *   PRISM : rho0 on the half-open box [lo, hi), else 0.
- *   VOXEL : grid[ix + nx (iy + ny iz)] (float32, x fastest, DEVICE pointer)
+ *   VOXEL : grid[ix + nx (iy + ny iz)] (float32, x fastest; DEVICE pointer,
+ *           or HOST for mcgrav_solve)
  *           on cells [origin + i spacing, origin + (i+1) spacing); 0 outside.
  * G is the gravitational constant of the unit system (1 for nondimensional
  * problems, 6.67430e-11 in SI). */
@@ -108,7 +109,8 @@ typedef enum { MCG_G_ZERO = 0, MCG_G_SPHERE = 1, MCG_G_PRISM = 2, MCG_G_TABLE = 
  *   SPHERE: the analytic potential of the density's sphere.
  *   PRISM : the analytic potential of the density's prism (Nagy's corner
  *           function, the closed form the paper compares against).
- *   TABLE : six node-centred float32 tables (DEVICE pointer) of nv x nu
+ *   TABLE : six node-centred float32 tables (DEVICE pointer; HOST accepted
+ *           by mcgrav_solve) of nv x nu
  *           nodes each (u fastest) in face order -x,+x,-y,+y,-z,+z; face
  *           +-x is tabulated over (y, z), +-y over (x, z), +-z over (x, y),
  *           nodes spanning the face edge to edge; read bilinearly.
@@ -189,7 +191,9 @@ MCG_API const char* mcg_version(void);
 /* mcgrav_solve: estimates Phi and dPhi/dz at S stations from `paths` walks
  * each (paths 0 .. paths-1 of each station's stream).
  *   stations : HOST, S x 3 row-major (x, y, z).
- *   density, boundary : grid / faces are DEVICE pointers when used.
+ *   density, boundary : grid / faces in DEVICE or HOST memory (host arrays
+ *            are copied into the call's workspace; the device-level entry
+ *            points below take device pointers only).
  *   out      : HOST arrays of length S.
  * Blocking.  Allocates a device workspace of at most mcg_workspace_bytes(S,
  * batch) for the duration of the call.  With several batches, consecutive

@@ -39,8 +39,18 @@ int set_error(int code, const char* fmt, ...)
     return code;
 }
 
-// Checks the problem description and fills the launch parameters (without
-// the work list, which the caller adds).
+// True when p is host memory (pageable or pinned): mcgrav_solve then stages
+// the array in its workspace instead of letting kernels read it.
+bool host_memory(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
 // mcgrav_solve's workspace: a shared part (stations, station states, status
 // word, finalized results) and one or two per-launch sets (per-path values,
 // work counter, walk scratch) -- two when the solve has several batches, so
@@ -126,6 +136,8 @@ cudaError_t reset_walk(const WalkParams& P, cudaStream_t st)
     return e;
 }
 
+// Checks the problem description and fills the launch parameters (without
+// the work list, which the caller adds).
 int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B, double dt, uint64_t seed,
                 const mcg_options* o, WalkParams& P)
 {
@@ -494,7 +506,16 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     const int64_t nbatch = (paths + batch - 1) / batch;
     const int nsets = nbatch >= 2 ? 2 : 1;
     const size_t set_bytes = solve_set_bytes(S, batch);
-    const size_t bytes = solve_shared_bytes(S) + (size_t)nsets * set_bytes;
+    // a voxel grid or boundary tables in host memory are staged in the workspace
+    mcg_density den = *density;
+    mcg_boundary bnd = *boundary;
+    size_t grid_bytes = 0, faces_bytes = 0;
+    if (den.kind == MCG_RHO_VOXEL && den.grid && host_memory(den.grid))
+        grid_bytes = (size_t)den.nx * (size_t)den.ny * (size_t)den.nz * sizeof(float);
+    if (bnd.kind == MCG_G_TABLE && bnd.faces && host_memory(bnd.faces))
+        faces_bytes = 6 * (size_t)bnd.nu * (size_t)bnd.nv * sizeof(float);
+    const size_t bytes = solve_shared_bytes(S) + (size_t)nsets * set_bytes + align256(grid_bytes) +
+                         align256(faces_bytes);
     char* ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, bytes);
     if (e != cudaSuccess) {
@@ -531,6 +552,9 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
         set[k].work = (void*)q;
         q += mcg_walk_work_bytes(S, batch, MCG_MIXED);
     }
+    float* d_grid = grid_bytes ? (float*)q : nullptr;
+    q += align256(grid_bytes);
+    float* d_faces = faces_bytes ? (float*)q : nullptr;
 
     double* h_res = new double[6 * s_];
     int32_t h_status = 0;
@@ -538,10 +562,14 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     do {
         if ((e = cudaMemcpyAsync(d_st, stations, s_ * 3 * sizeof(double), cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemsetAsync(d_state, 0, s_ * sizeof(mcg_station_state), st)) ||
-            (e = cudaMemsetAsync(d_status, 0, 256, st))) {
+            (e = cudaMemsetAsync(d_status, 0, 256, st)) ||
+            (grid_bytes && (e = cudaMemcpyAsync(d_grid, den.grid, grid_bytes, cudaMemcpyHostToDevice, st))) ||
+            (faces_bytes && (e = cudaMemcpyAsync(d_faces, bnd.faces, faces_bytes, cudaMemcpyHostToDevice, st)))) {
             rc = cuda_fail(e, "workspace initialisation");
             break;
         }
+        if (grid_bytes) den.grid = d_grid;
+        if (faces_bytes) bnd.faces = d_faces;
         // The batches (counter and pool reset, walk, exit evaluation,
         // reduction), then the finalize.  With several batches, batch j runs
         // on stream j % 2 with buffer set j % 2, so one batch's exit-time
@@ -572,7 +600,7 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
             const int64_t nb = (paths - p0) < batch ? (paths - p0) : batch;
             const int k = (int)(j % nsets);
             ro.stream = qs[k];
-            rc = mcg_walk(domain, density, boundary, d_st, S, p0, nb, dt, seed, &ro, set[k].u, set[k].d,
+            rc = mcg_walk(domain, &den, &bnd, d_st, S, p0, nb, dt, seed, &ro, set[k].u, set[k].d,
                           set[k].steps, set[k].work, d_status, set[k].counter);
             if (rc == MCG_OK && j > 0 && (e = cudaStreamWaitEvent(qs[k], ev_red, 0)))
                 rc = cuda_fail(e, "reduction order");

@@ -191,3 +191,21 @@ def test_voxel_survey_against_the_exact_potential():
         assert np.all(np.abs(r["u"] - phi) < 4 * r["se_u"] + 5e-3 * np.abs(phi))
         devs[step] = float(np.mean(np.abs(r["u"] - phi) / np.abs(phi)))
     assert devs[5.0] < 0.75 * devs[10.0], devs
+
+
+def test_mcgrav_solve_takes_host_or_device_model_arrays(voxel_inputs):
+    """mcgrav_solve accepts the voxel grid and the boundary tables in host
+    memory (staged into its workspace) as well as on the device: the same
+    walks either way.  Path counts and steps are identical; with a voxel
+    density the single-precision partial sums are flushed at schedule-
+    dependent steps, so the statistics agree to rounding (1e-5 relative)."""
+    w, grid, faces = voxel_inputs
+    st = w.stations[[5, 77]]
+    opts = M.options(w, precision=M.MCG_MIXED)
+    host = M.mcgrav_solve(M.problem(w, grid=grid, faces=faces), st, 2048, w.dt, w.seed, opts)
+    gd, fd = torch.from_numpy(grid).cuda(), torch.from_numpy(faces).cuda()
+    dev = M.mcgrav_solve(M.problem(w, grid=gd, faces=fd), st, 2048, w.dt, w.seed, opts)
+    for k in ("n_paths", "path_steps"):
+        assert np.array_equal(getattr(host, k), getattr(dev, k)), k
+    for k in ("u", "gz", "se_u", "se_gz"):
+        np.testing.assert_allclose(getattr(host, k), getattr(dev, k), rtol=1e-5, err_msg=k)
