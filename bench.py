@@ -316,6 +316,16 @@ def run_ours(args):
     stations_per_s = paths_per_s / float(np.mean(n_req))
     mean_steps_per_path = path_steps_local / (S * Bp * args.steps)
 
+    # end to end through the public API on every rank (independent seeds per
+    # rank); the whole-job value is all ranks' path-steps over the slowest rank
+    e2e = None
+    if not args.skip_e2e:
+        barrier(world)
+        e2e = e2e_server(M, w, Bp, args.steps, seed0=1000 + 100_000 * rank)
+        e2e_steps, = allreduce([e2e.pop("path_steps")], _sum_op(world), world)
+        e2e_s, = allreduce([e2e.pop("seconds")], _max_op(world), world)
+        e2e["value"] = e2e_steps / e2e_s
+
     out = {}
     if rank == 0:
         # roofline of the dominant kernel (the mixed walk): model lane-instructions
@@ -337,12 +347,15 @@ def run_ours(args):
                            "launch_time": "timed region / K (two-stream pipeline)",
                            "launch_event_ms_mean": statistics.mean(walk_ms),
                            "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (recipe unit counts)"}
-        if not args.skip_fp64:
+        if e2e is not None:
+            out["e2e"] = e2e
+        # single-GPU extras: the FP64 comparison, the blocking one-call API and
+        # the CPU oracle baseline
+        if not args.skip_fp64 and world == 1:
             out["fp64_walk"] = fp64_comparison(M, w, dev)
-        if not args.skip_e2e:
-            out["e2e"] = e2e_server(M, w, Bp, args.steps)
+        if not args.skip_e2e and world == 1:
             out["e2e_blocking_solve"] = e2e_solve(M, w, Bp, max(1, min(args.steps, 3)))
-        if not args.skip_cpu:
+        if not args.skip_cpu and world == 1:
             rate, dt, cores, _ = cpu_oracle_rate(w, args.cpu_paths)
             n1 = max(1, args.cpu_paths // 16)
             rate1, dt1, _, _ = cpu_oracle_rate(w, n1, p0=args.cpu_paths, threads=1)
@@ -442,7 +455,7 @@ def e2e_solve(M, w, Bp, steps):
             "d2h_bytes_per_step": S * 6 * 8 + 4, "steps": steps, "api": "mcgrav_solve (blocking, one stream)"}
 
 
-def e2e_server(M, w, Bp, steps):
+def e2e_server(M, w, Bp, steps, seed0=1000):
     """The asynchronous public API end to end: each step is one request
     (mcg_submit with HOST stations) of the 30 stations x Bp paths, walked in
     one round whose station results are copied back to HOST memory; the step
@@ -462,7 +475,7 @@ def e2e_server(M, w, Bp, steps):
         M.mcg_request_free(warm)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reqs = [M.mcg_submit(sv, model, w.stations, 1e-12, 1000 + k) for k in range(steps)]
+        reqs = [M.mcg_submit(sv, model, w.stations, 1e-12, seed0 + k) for k in range(steps)]
         total_steps = 0.0
         for rq in reqs:
             rc, out = M.mcg_wait(rq, S)
@@ -476,7 +489,8 @@ def e2e_server(M, w, Bp, steps):
         M.mcg_model_destroy(model)
     return {"value": total_steps / t, "unit": UNIT, "h2d_bytes_per_step": S * 3 * 8,
             "d2h_bytes_per_step": S * 6 * 8 + 4, "steps": steps,
-            "api": "mcg_submit / mcg_wait (server; one request per step, one stream per request)"}
+            "api": "mcg_submit / mcg_wait (server; one request per step, one stream per request)",
+            "path_steps": total_steps, "seconds": t}
 
 
 def run_serving(args):
