@@ -100,6 +100,12 @@ typedef struct {
     const float* grid;
     int64_t nx, ny, nz;
     double origin[3], spacing[3];
+    const float* zpack;      /* VOXEL, optional DEVICE array from mcg_voxel_pack
+                                (NULL: not used).  The mixed walk then reads the
+                                densities of its three common-random-number
+                                copies (z, z + h, z - h) with one 16-byte load
+                                per step instead of three 4-byte loads; used when
+                                h <= spacing[2] / 2.  Same values, same results. */
 } mcg_density;
 
 typedef enum { MCG_G_ZERO = 0, MCG_G_SPHERE = 1, MCG_G_PRISM = 2, MCG_G_TABLE = 3, MCG_G_POLY = 4 } mcg_g_kind;
@@ -121,6 +127,10 @@ typedef struct {
     const float* faces;
     int32_t nu, nv;
     double poly[11];
+    const float* quads;      /* TABLE, optional DEVICE array from mcg_table_pack
+                                (NULL: not used): the four corner values of every
+                                table cell side by side, read with one 16-byte
+                                load per exit.  Same values, same results.      */
 } mcg_boundary;
 
 typedef enum { MCG_FP64 = 0, MCG_MIXED = 1 } mcg_precision;
@@ -158,6 +168,14 @@ typedef struct {
                                 not depend on it for piecewise-constant densities;
                                 for a voxel grid the single-precision partial sums
                                 are flushed at other steps (rounding only).       */
+    int32_t fault_unpublished;/* failure-detection test hook, 0..255 (default 0):
+                                the launch starts with this many migration-pool
+                                slots reserved but never published, as if a warp
+                                had died between its reservation and its store.
+                                A warp that claims one waits a bounded time
+                                (about 0.1-1 s) for it, gives up, and the walk
+                                reports MCG_ERR_TIMEOUT; every real walk still
+                                finishes.  Needs the mixed walk with migrate = 1. */
 } mcg_options;
 
 /* Per-station outputs (caller-owned, length S; any pointer may be NULL). */
@@ -195,8 +213,11 @@ MCG_API const char* mcg_version(void);
  *            are copied into the call's workspace; the device-level entry
  *            points below take device pointers only).
  *   out      : HOST arrays of length S.
- * Blocking.  Allocates a device workspace of at most mcg_workspace_bytes(S,
- * batch) for the duration of the call.  With several batches, consecutive
+ * Blocking.  Allocates a device workspace for the duration of the call:
+ * mcg_workspace_bytes(S, batch), plus the packed copies of a voxel grid and
+ * of boundary tables (mcg_voxel_pack_bytes, mcg_table_pack_bytes) unless the
+ * caller passes them, plus the grid and tables themselves when they are in
+ * host memory.  With several batches, consecutive
  * batches alternate between two streams (the caller's and one of the
  * call's own) so that one batch's exit-time tail runs beside the next
  * batch; the reductions stay in batch order, so the result does not depend
@@ -225,8 +246,14 @@ MCG_API int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, c
  *                 256-byte aligned.
  *   status_dev  : DEVICE int32, OR-ed with (1 << status) for every path that
  *                 hit the step cap, started outside Omega or produced a
- *                 non-finite value; the caller zeroes it.
+ *                 non-finite value, and for a cancel or a bounded wait that
+ *                 gave up (MCG_ERR_TIMEOUT); the caller zeroes it.
  *   counter_dev : DEVICE uint64 work counter, zeroed by this call.
+ * Items that do not finish (cancelled, never started, capped, lost after a
+ * timeout, station outside Omega) read pp_u = pp_d = NaN; pp_steps is 0 for
+ * items never started.  The call marks every item "no result" before the
+ * launch (a stream-ordered fill of 8 B per item, plus 24 B of exit records
+ * per item for the mixed walk), so nothing is read from an earlier launch.
  * Allocates nothing. */
 MCG_API int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
              const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
@@ -253,8 +280,12 @@ MCG_API size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision);
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
  *   - All calls share the one array and it keeps the last call's contents;
- *     the call zeroes the counter itself.  Calls that overlap on the GPU
- *     (other streams, other threads) race on it: serialise them.
+ *     the call zeroes the counter and marks its exit records "no result"
+ *     itself, so items that do not finish read NaN as with mcg_walk.  Calls
+ *     that overlap on the GPU (other streams, other threads) race on it:
+ *     serialise them.
+ *   - The array's address is cached per device after the first call; a
+ *     device reset (cudaDeviceReset) after that call is not supported.
  *   - opts->migrate is ignored: the array holds no migration pool, so each
  *     warp keeps its walks to the end (same results, longer exit-time tail).
  * Asynchronous on opts->stream like mcg_walk. */
@@ -406,6 +437,37 @@ MCG_API int mcg_request_free(mcg_request* r);
 /* Heterogeneous model set-up (once per model, outside the walk).            */
 /* ---------------------------------------------------------------------- */
 
+/* ---------------------------------------------------------------------- */
+/* Packed copies of the model arrays for the walk's 16-byte loads.          */
+/* ---------------------------------------------------------------------- */
+/* The walk reads the voxel grid once per step and copy, and a boundary table
+ * once per exit, at scattered positions: every read costs a cache sector of
+ * its own.  The packed copies put what one step (or one exit) needs side by
+ * side, so one aligned 16-byte load replaces three (or four) 4-byte loads.
+ * Build them once per model (like the model itself) and pass them in
+ * mcg_density.zpack / mcg_boundary.quads.  mcgrav_solve and mcg_model_create
+ * build them on their own. */
+
+/* Bytes of mcg_voxel_pack's output: 16 nx ny (nz + 2). */
+MCG_API size_t mcg_voxel_pack_bytes(int64_t nx, int64_t ny, int64_t nz);
+
+/* mcg_voxel_pack: out[((iz + 1) ny + iy) nx + ix] = (rho(ix, iy, iz - 1),
+ * rho(ix, iy, iz), rho(ix, iy, iz + 1), 0) as four floats, for iz = -1 .. nz,
+ * with rho = 0 outside the grid.  density: VOXEL with a DEVICE grid.
+ * out: DEVICE, mcg_voxel_pack_bytes, 16-byte aligned.  Asynchronous on
+ * `stream`.  Allocates nothing. */
+MCG_API int mcg_voxel_pack(const mcg_density* density, float* out, void* stream);
+
+/* Bytes of mcg_table_pack's output: 16 * 6 (nu - 1) (nv - 1). */
+MCG_API size_t mcg_table_pack_bytes(int32_t nu, int32_t nv);
+
+/* mcg_table_pack: out[(f (nv - 1) + iv) (nu - 1) + iu] = (t(iu, iv),
+ * t(iu + 1, iv), t(iu, iv + 1), t(iu + 1, iv + 1)) of face f's table t (the
+ * MCG_G_TABLE layout).  boundary: TABLE with DEVICE faces.  out: DEVICE,
+ * mcg_table_pack_bytes, 16-byte aligned.  Asynchronous on `stream`.
+ * Allocates nothing. */
+MCG_API int mcg_table_pack(const mcg_boundary* boundary, float* out, void* stream);
+
 /* Bytes of device scratch mcg_grf_density needs for an nx x ny x nz grid. */
 MCG_API size_t mcg_grf_work_bytes(int64_t nx, int64_t ny, int64_t nz);
 
@@ -435,6 +497,45 @@ MCG_API int mcg_grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, d
  * Asynchronous on `stream`.  Allocates nothing. */
 MCG_API int mcg_boundary_tables(const mcg_domain* domain, const mcg_density* density, int32_t nu, int32_t nv,
                                 double near_cells, float* faces_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Exact field of the density models (the reference the walk is checked     */
+/* against).                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* mcg_field: the exact potential Phi (Delta Phi = 4 pi G rho, Phi -> 0 far
+ * away) and its vertical derivative dPhi/dz of the density model at n
+ * points, the closed forms the paper compares its stochastic solution with
+ * (Sec. 4.2: the analytic field of the prism):
+ *   SPHERE: -G M / r outside, -G M (3 a^2 - r^2) / (2 a^3) inside.
+ *   PRISM : Nagy's corner function F over the eight corners,
+ *           Phi = -G rho0 [[[F]]], dPhi/dz = G rho0 [[[dF/dz]]].
+ *   VOXEL : the sum of every voxel's prism field, regrouped by grid node:
+ *           Phi(x) = -G sum_nodes w_n F(node - x), where w_n adds the
+ *           densities of the (up to eight) cells sharing the node with the
+ *           sign of that corner in each cell's prism sum.  Double precision
+ *           with compensated sums; one block per point, (nx+1)(ny+1)(nz+1)
+ *           corner evaluations per point (about 0.5 ms per point on a GB300
+ *           for a 128 x 128 x 64 grid).
+ *   NONE  : 0.
+ * points_dev: DEVICE, n x 3 row-major.  phi_dev, gz_dev: DEVICE, length n
+ * (either may be NULL).  density->grid: DEVICE.  Asynchronous on `stream`.
+ * Allocates nothing. */
+MCG_API int mcg_field(const mcg_density* density, const double* points_dev, int64_t n, double* phi_dev,
+                      double* gz_dev, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Measured peaks (the denominators of the walk's roofline).                */
+/* ---------------------------------------------------------------------- */
+
+/* mcg_issue_probe: the lane-instruction rate the current GPU sustains on long
+ * runs of independent single-precision FMAs (kind 0) or of FMAs and
+ * three-input xors side by side (kind 1, the two pipes the walk's generator
+ * and transform use), one persistent launch over every SM, timed with CUDA
+ * events after a warm-up launch.  No counterpart in the paper: it measures
+ * the hardware the walk runs on.  lane_ops_per_s, seconds: HOST (either may
+ * be NULL).  Blocking; allocates and frees 4 bytes of device memory. */
+MCG_API int mcg_issue_probe(int32_t kind, int32_t iters, double* lane_ops_per_s, double* seconds);
 
 #ifdef __cplusplus
 }

@@ -84,6 +84,7 @@ void preload_kernels()
     if (bit && (loaded.load(std::memory_order_relaxed) & bit)) return;
     preload_walk_kernels();
     preload_reduce_kernels();
+    preload_field_kernels();
     loaded.fetch_or(bit, std::memory_order_release);
 }
 
@@ -127,11 +128,23 @@ void bind_work(WalkParams& P, void* work, bool migrate)
 
 cudaError_t reset_walk(const WalkParams& P, cudaStream_t st)
 {
+    const size_t T = (size_t)P.total;
     cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st);
+    // Items that never finish (cancel, a lost walk) must not read an earlier
+    // launch's values: steps 0, and "no record" for every copy (mixed walk) or
+    // NaN per-path values (FP64 walk, which writes them directly).
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.pp_steps, 0, T * sizeof(int64_t), st);
+    if (e == cudaSuccess && P.drec) e = cudaMemsetAsync(P.drec, 0xFF, 3 * T * sizeof(double), st);
+    if (e == cudaSuccess && !P.drec) e = cudaMemsetAsync(P.pp_u, 0xFF, T * sizeof(double), st);
+    if (e == cudaSuccess && !P.drec) e = cudaMemsetAsync(P.pp_d, 0xFF, T * sizeof(double), st);
     if (e == cudaSuccess && P.pool) {
         // flags and counters are adjacent: one memset covers both
         const size_t bytes = (size_t)((unsigned char*)P.pool_ctr - (unsigned char*)P.pool_ready) + 256;
         e = cudaMemsetAsync(P.pool_ready, 0, bytes, st);
+        // test hook: slots counted as reserved whose ready flag nobody sets
+        // (the low byte of the little-endian reservation counter)
+        if (e == cudaSuccess && P.fault_unpublished)
+            e = cudaMemsetAsync(P.pool_ctr, (int)P.fault_unpublished, 1, st);
     }
     return e;
 }
@@ -249,6 +262,10 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     P.faces = B->faces;
     P.nu = B->nu;
     P.nv = B->nv;
+    if (B->kind == MCG_G_TABLE && B->quads) {
+        if ((uintptr_t)B->quads % 16 != 0) return set_error(MCG_ERR_ARG, "boundary quads must be 16-byte aligned");
+        P.tq = (const float4*)B->quads;
+    }
     for (int i = 0; i < 11; ++i) P.poly[i] = B->poly[i];
 
     P.dt = dt;
@@ -257,6 +274,12 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     P.two_pi_G = 2.0 * kPi * R->G;
     P.sd_f = (float)P.sd;
     P.h_f = (float)P.h;
+    if (R->kind == MCG_RHO_VOXEL && R->zpack) {
+        if ((uintptr_t)R->zpack % 16 != 0) return set_error(MCG_ERR_ARG, "voxel zpack must be 16-byte aligned");
+        // one packed entry covers the copies' layers only while h <= half a cell
+        if (!(P.h_f * P.inv_sp_f[2] <= 0.5f)) return set_error(MCG_ERR_ARG, "zpack needs h <= spacing[2] / 2");
+        P.zq = (const float4*)R->zpack;
+    }
     P.lnscale_f = (float)(-2.0 * std::log(2.0) * P.sd * P.sd);
     P.crn = o->crn_gz ? 1 : 0;
     P.clip = o->clip ? 1 : 0;
@@ -293,6 +316,9 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
         }
     }
     P.max_steps = o->max_steps;
+    if (o->fault_unpublished < 0 || o->fault_unpublished > 255)
+        return set_error(MCG_ERR_ARG, "fault_unpublished must be in [0, 255]");
+    P.fault_unpublished = (uint32_t)o->fault_unpublished;
     P.key0 = (uint32_t)seed;
     P.key1 = (uint32_t)(seed >> 32);
     P.cancel = o->cancel;
@@ -319,13 +345,18 @@ int check_station(const WalkParams& P, const double* x, int64_t s)
     return MCG_OK;
 }
 
+// Status of a walk from its device status word.  Every nonzero word is an
+// error: an unknown bit maps to MCG_ERR_CUDA rather than to success.
 int status_from_bits(int bits)
 {
+    if (bits == 0) return MCG_OK;
     if (bits & (1 << MCG_ERR_ARG)) return set_error(MCG_ERR_ARG, "a station lies on or outside the domain");
+    if (bits & (1 << MCG_ERR_TIMEOUT))
+        return set_error(MCG_ERR_TIMEOUT, "a bounded wait on a migrated walk gave up (that walk reads NaN)");
+    if (bits & (1 << MCG_ERR_CANCELLED)) return set_error(MCG_ERR_CANCELLED, "cancelled");
     if (bits & (1 << MCG_ERR_STEP_CAP)) return set_error(MCG_ERR_STEP_CAP, "a path exceeded max_steps");
     if (bits & (1 << MCG_ERR_NONFINITE)) return set_error(MCG_ERR_NONFINITE, "a per-path value was not finite");
-    if (bits & (1 << MCG_ERR_CANCELLED)) return set_error(MCG_ERR_CANCELLED, "cancelled");
-    return MCG_OK;
+    return set_error(MCG_ERR_CUDA, "unknown walk status bits 0x%x", (unsigned)bits);
 }
 
 }  // namespace mcg
@@ -400,6 +431,7 @@ void mcg_options_default(mcg_options* o)
     o->refill_min = 1;
     o->graph = 1;
     o->migrate = 1;
+    o->fault_unpublished = 0;
 }
 
 const char* mcg_last_error(void) { return g_err; }
@@ -509,13 +541,17 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     // a voxel grid or boundary tables in host memory are staged in the workspace
     mcg_density den = *density;
     mcg_boundary bnd = *boundary;
-    size_t grid_bytes = 0, faces_bytes = 0;
+    size_t grid_bytes = 0, faces_bytes = 0, zpack_bytes = 0, quad_bytes = 0;
     if (den.kind == MCG_RHO_VOXEL && den.grid && host_memory(den.grid))
         grid_bytes = (size_t)den.nx * (size_t)den.ny * (size_t)den.nz * sizeof(float);
     if (bnd.kind == MCG_G_TABLE && bnd.faces && host_memory(bnd.faces))
         faces_bytes = 6 * (size_t)bnd.nu * (size_t)bnd.nv * sizeof(float);
+    // packed copies for the walk's 16-byte loads, unless the caller brought them
+    if (den.kind == MCG_RHO_VOXEL && !den.zpack && P.h_f * P.inv_sp_f[2] <= 0.5f)
+        zpack_bytes = mcg_voxel_pack_bytes(den.nx, den.ny, den.nz);
+    if (bnd.kind == MCG_G_TABLE && !bnd.quads) quad_bytes = mcg_table_pack_bytes(bnd.nu, bnd.nv);
     const size_t bytes = solve_shared_bytes(S) + (size_t)nsets * set_bytes + align256(grid_bytes) +
-                         align256(faces_bytes);
+                         align256(faces_bytes) + align256(zpack_bytes) + align256(quad_bytes);
     char* ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, bytes);
     if (e != cudaSuccess) {
@@ -555,6 +591,10 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     float* d_grid = grid_bytes ? (float*)q : nullptr;
     q += align256(grid_bytes);
     float* d_faces = faces_bytes ? (float*)q : nullptr;
+    q += align256(faces_bytes);
+    float* d_zpack = zpack_bytes ? (float*)q : nullptr;
+    q += align256(zpack_bytes);
+    float* d_quads = quad_bytes ? (float*)q : nullptr;
 
     double* h_res = new double[6 * s_];
     int32_t h_status = 0;
@@ -570,6 +610,14 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
         }
         if (grid_bytes) den.grid = d_grid;
         if (faces_bytes) bnd.faces = d_faces;
+        if (d_zpack) {
+            if ((rc = voxel_pack(&den, d_zpack, st))) break;
+            den.zpack = d_zpack;
+        }
+        if (d_quads) {
+            if ((rc = table_pack(&bnd, d_quads, st))) break;
+            bnd.quads = d_quads;
+        }
         // The batches (counter and pool reset, walk, exit evaluation,
         // reduction), then the finalize.  With several batches, batch j runs
         // on stream j % 2 with buffer set j % 2, so one batch's exit-time
@@ -740,6 +788,28 @@ int mcg_boundary_tables(const mcg_domain* domain, const mcg_density* density, in
     return boundary_tables(domain, density, nu, nv, near_cells, faces_out, (cudaStream_t)stream);
 }
 
+size_t mcg_voxel_pack_bytes(int64_t nx, int64_t ny, int64_t nz)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
+    return (size_t)16 * (size_t)nx * (size_t)ny * (size_t)(nz + 2);
+}
+
+int mcg_voxel_pack(const mcg_density* density, float* out, void* stream)
+{
+    return voxel_pack(density, out, (cudaStream_t)stream);
+}
+
+size_t mcg_table_pack_bytes(int32_t nu, int32_t nv)
+{
+    if (nu < 2 || nv < 2) return 0;
+    return (size_t)16 * 6 * (size_t)(nu - 1) * (size_t)(nv - 1);
+}
+
+int mcg_table_pack(const mcg_boundary* boundary, float* out, void* stream)
+{
+    return table_pack(boundary, out, (cudaStream_t)stream);
+}
+
 int64_t mcg_walk_static_max_items(void) { return static_max_items(); }
 
 int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
@@ -780,9 +850,11 @@ int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const 
         P.drec = (double*)(base + 256 + align256(n * 3 * 8 * sizeof(float)));
     }
     cudaStream_t st = (cudaStream_t)opts->stream;
-    // the counter must start at zero; the exit records are written before use
-    e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(static counter)");
+    // the counter starts at zero and every item at "no result", so that an
+    // item that does not finish (cancel) never reads the last call's records
+    // left in the shared array; there is no migration pool here
+    e = reset_walk(P, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(static scratch)");
     e = launch_walk(P, opts->precision, opts->block ? opts->block : 128, st);
     if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     return MCG_OK;

@@ -163,6 +163,23 @@ __device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, 
         ra = (inxy && za >= 0.f && za < (float)P.nz) ? __ldg(P.grid + base + plane * (int)za) : 0.0f;
         rb = (inxy && zb >= 0.f && zb < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zb) : 0.0f;
         rc = (inxy && zc >= 0.f && zc < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zc) : 0.0f;
+    } else if constexpr (RHO == kRhoVoxelPacked) {
+        // The same cells as above, read through the packed grid: the copies'
+        // layers zb, zc differ from za by at most one (h <= half a cell), and
+        // the 16-byte entry of layer za holds layers za-1, za, za+1 (0 outside
+        // the grid), so one load serves all three copies.
+        const float tx = floorf(__fmul_rn(__fsub_rn(x, P.org_f[0]), P.inv_sp_f[0]));
+        const float ty = floorf(__fmul_rn(__fsub_rn(y, P.org_f[1]), P.inv_sp_f[1]));
+        const float za = floorf(__fmul_rn(__fsub_rn(z, P.org_f[2]), P.inv_sp_f[2]));
+        const float zb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
+        const float zc = floorf(__fmul_rn(__fsub_rn(__fsub_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
+        const bool in = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny && za >= -1.f &&
+                        za <= (float)P.nz;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) q = __ldg(P.zq + ((int)za + 1) * P.ny * P.nx + (int)ty * P.nx + (int)tx);
+        ra = q.y;
+        rb = zb > za ? q.z : q.y;
+        rc = zc < za ? q.x : q.y;
     } else {
         ra = rb = rc = 0.0f;
     }
@@ -260,8 +277,20 @@ __device__ __forceinline__ double table_value(const WalkParams& P, int face, con
     const double fv = fmin(fmax(floor(tv), 0.0), (double)(P.nv - 2));
     const int iu = (int)fu, iv = (int)fv;
     const double au = tu - fu, av = tv - fv;
-    const float* r0 = t + (int64_t)P.nu * iv + iu;
-    const double f00 = __ldg(r0), f10 = __ldg(r0 + 1), f01 = __ldg(r0 + P.nu), f11 = __ldg(r0 + P.nu + 1);
+    double f00, f10, f01, f11;
+    if (P.tq) {  // the cell's four corners in one 16-byte load
+        const float4 c = __ldg(P.tq + ((int64_t)face * (P.nv - 1) + iv) * (P.nu - 1) + iu);
+        f00 = c.x;
+        f10 = c.y;
+        f01 = c.z;
+        f11 = c.w;
+    } else {
+        const float* r0 = t + (int64_t)P.nu * iv + iu;
+        f00 = __ldg(r0);
+        f10 = __ldg(r0 + 1);
+        f01 = __ldg(r0 + P.nu);
+        f11 = __ldg(r0 + P.nu + 1);
+    }
     return (1.0 - au) * (1.0 - av) * f00 + au * (1.0 - av) * f10 + (1.0 - au) * av * f01 + au * av * f11;
 }
 

@@ -34,9 +34,11 @@ struct WalkParams {
     int32_t nx, ny, nz;
     double org[3], sp[3];          // voxel origin / spacing (absolute)
     float org_f[3], inv_sp_f[3];   // origin relative to cen, 1/spacing
+    const float4* zq;              // packed voxel grid (layers iz-1, iz, iz+1 per cell), or null
     // boundary data
     int32_t g_kind;
     const float* faces;
+    const float4* tq;              // packed table cells (four corners), or null
     int32_t nu, nv;
     double poly[11];
     // walk
@@ -67,7 +69,17 @@ struct WalkParams {
     uint32_t* pool_ready;
     unsigned long long* pool_ctr;
     unsigned long long pool_cap;
+    uint32_t fault_unpublished;    // host side: pool slots reserved and never published
 };
+
+// Exit-record marker of an item without a result (never started, cancelled,
+// capped, lost, station outside Omega): the all-ones double, a NaN pattern
+// that no floating-point operation produces, written by a byte fill.
+constexpr long long kNoRecordBits = -1LL;
+
+// Kernel-template tag of the voxel density read through the packed grid
+// (WalkParams::zq); not a public density kind.
+constexpr int kRhoVoxelPacked = 4;
 
 constexpr size_t kPoolEntryBytes = 80;
 constexpr unsigned long long kPoolMaxSlots = 1ull << 19;
@@ -84,7 +96,9 @@ void bind_work(WalkParams& P, void* work, bool migrate);
 // mcgrav_solve's workspace parts (mcg_api.cu).
 size_t solve_shared_bytes(int64_t S);
 size_t solve_set_bytes(int64_t S, int64_t batch);
-// Zeroes the work counter and, with migration, the pool's flags and counters.
+// Zeroes the work counter, marks every item "no result" (exit records of the
+// mixed walk, per-path values of the FP64 walk, steps 0) and, with migration,
+// zeroes the pool's flags and counters.
 cudaError_t reset_walk(const WalkParams& P, cudaStream_t st);
 
 // Kernel launchers (mcg_walk.cu).
@@ -102,6 +116,10 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 cudaError_t launch_normals(uint64_t seed, uint32_t s, uint32_t p, uint32_t b0, int64_t nblocks, int precision,
                            void* out, cudaStream_t st);
 
+// Packed model arrays (mcg_setup.cu).
+int voxel_pack(const mcg_density* rho, float* out, cudaStream_t st);
+int table_pack(const mcg_boundary* b, float* out, cudaStream_t st);
+
 // Set-up launchers (mcg_setup.cu).
 int grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, double sigma_vox, double amp, float* grid_out,
                 double* work, cudaStream_t st);
@@ -116,6 +134,7 @@ int boundary_tables(const mcg_domain* d, const mcg_density* rho, int32_t nu, int
 // preload_kernels() does it once per device (mcg_api.cu).
 void preload_walk_kernels();    // mcg_walk.cu
 void preload_reduce_kernels();  // mcg_reduce.cu
+void preload_field_kernels();   // mcg_field.cu
 void preload_kernels();
 
 // Thread-local error message (mcg_api.cu).

@@ -86,6 +86,8 @@ struct mcg_model {
     double h = 0.0;
     float* grid = nullptr;   // owned device copy
     float* faces = nullptr;  // owned device copy
+    float* zpack = nullptr;  // owned packed grid (mcg_voxel_pack)
+    float* quads = nullptr;  // owned packed tables (mcg_table_pack)
 };
 
 struct mcg_request {
@@ -435,6 +437,8 @@ int mcg_model_create(const mcg_domain* domain, const mcg_density* density, const
     m->bnd = *boundary;
     m->dt = dt;
     m->h = h;
+    m->den.zpack = nullptr;  // the model never keeps a caller's array: it packs its own copy
+    m->bnd.quads = nullptr;
     cudaError_t e = cudaSuccess;
     if (density->kind == MCG_RHO_VOXEL) {
         const size_t n = (size_t)density->nx * density->ny * density->nz;
@@ -456,6 +460,38 @@ int mcg_model_create(const mcg_domain* domain, const mcg_density* density, const
         }
         m->bnd.faces = m->faces;
     }
+    // packed copies for the walk's 16-byte loads (the grid one only while the
+    // copies' layers stay within one cell of each other: h <= spacing_z / 2)
+    if (density->kind == MCG_RHO_VOXEL && P.h_f * P.inv_sp_f[2] <= 0.5f) {
+        const size_t b = mcg_voxel_pack_bytes(density->nx, density->ny, density->nz);
+        if ((e = cudaMalloc(&m->zpack, b))) {
+            mcg_model_destroy(m);
+            return set_error(e == cudaErrorMemoryAllocation ? MCG_ERR_OOM : MCG_ERR_CUDA, "model zpack: %s",
+                             cudaGetErrorString(e));
+        }
+        if ((rc = voxel_pack(&m->den, m->zpack, 0))) {
+            mcg_model_destroy(m);
+            return rc;
+        }
+        m->den.zpack = m->zpack;
+    }
+    if (boundary->kind == MCG_G_TABLE) {
+        const size_t b = mcg_table_pack_bytes(boundary->nu, boundary->nv);
+        if ((e = cudaMalloc(&m->quads, b))) {
+            mcg_model_destroy(m);
+            return set_error(e == cudaErrorMemoryAllocation ? MCG_ERR_OOM : MCG_ERR_CUDA, "model quads: %s",
+                             cudaGetErrorString(e));
+        }
+        if ((rc = table_pack(&m->bnd, m->quads, 0))) {
+            mcg_model_destroy(m);
+            return rc;
+        }
+        m->bnd.quads = m->quads;
+    }
+    if ((e = cudaStreamSynchronize(0))) {
+        mcg_model_destroy(m);
+        return set_error(MCG_ERR_CUDA, "model set-up: %s", cudaGetErrorString(e));
+    }
     *out = m;
     return MCG_OK;
 }
@@ -465,6 +501,8 @@ int mcg_model_destroy(mcg_model* m)
     if (!m) return MCG_OK;
     if (m->grid) cudaFree(m->grid);
     if (m->faces) cudaFree(m->faces);
+    if (m->zpack) cudaFree(m->zpack);
+    if (m->quads) cudaFree(m->quads);
     delete m;
     return MCG_OK;
 }

@@ -208,7 +208,66 @@ __global__ void __launch_bounds__(kTableThreads) tables_kernel(const TableParams
     T.out[node] = (float)(-T.G * acc);
 }
 
+// Packed voxel grid: entry (iz + 1, iy, ix) = layers iz-1, iz, iz+1 of
+// column (ix, iy), 0 outside the grid, for iz = -1 .. nz.
+__global__ void voxel_pack_kernel(const float* __restrict__ g, int nx, int ny, int nz, float4* __restrict__ out)
+{
+    const int64_t n = (int64_t)nx * ny * (nz + 2);
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((int64_t)nx * ny)) - 1;
+    const int64_t col = (int64_t)iy * nx + ix, plane = (int64_t)nx * ny;
+    float v[3];
+    for (int d = 0; d < 3; ++d) {
+        const int k = iz - 1 + d;
+        v[d] = (k >= 0 && k < nz) ? g[col + plane * k] : 0.0f;
+    }
+    out[e] = make_float4(v[0], v[1], v[2], 0.0f);
+}
+
+// Packed tables: entry (f, iv, iu) = the corners (iu, iv), (iu+1, iv),
+// (iu, iv+1), (iu+1, iv+1) of cell (iu, iv) of face f.
+__global__ void table_pack_kernel(const float* __restrict__ t, int nu, int nv, float4* __restrict__ out)
+{
+    const int64_t cells = (int64_t)(nu - 1) * (nv - 1);
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 6 * cells) return;
+    const int f = (int)(e / cells);
+    const int64_t r = e % cells;
+    const int iu = (int)(r % (nu - 1)), iv = (int)(r / (nu - 1));
+    const float* row = t + (int64_t)f * nu * nv + (int64_t)iv * nu + iu;
+    out[e] = make_float4(row[0], row[1], row[nu], row[nu + 1]);
+}
+
 }  // namespace
+
+int voxel_pack(const mcg_density* rho, float* out, cudaStream_t st)
+{
+    if (!rho || !out) return set_error(MCG_ERR_ARG, "null argument");
+    if (rho->kind != MCG_RHO_VOXEL || !rho->grid) return set_error(MCG_ERR_ARG, "voxel_pack needs a voxel density");
+    if (rho->nx <= 0 || rho->ny <= 0 || rho->nz <= 0) return set_error(MCG_ERR_ARG, "voxel dims must be positive");
+    if ((double)rho->nx * (double)rho->ny * (double)(rho->nz + 2) >= 2147483647.0)
+        return set_error(MCG_ERR_ARG, "voxel grid too large to pack");
+    if ((uintptr_t)out % 16 != 0) return set_error(MCG_ERR_ARG, "packed grid must be 16-byte aligned");
+    const int64_t n = rho->nx * rho->ny * (rho->nz + 2);
+    voxel_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rho->grid, (int)rho->nx, (int)rho->ny,
+                                                                      (int)rho->nz, (float4*)out);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MCG_OK : set_error(MCG_ERR_CUDA, "voxel pack kernel: %s", cudaGetErrorString(e));
+}
+
+int table_pack(const mcg_boundary* b, float* out, cudaStream_t st)
+{
+    if (!b || !out) return set_error(MCG_ERR_ARG, "null argument");
+    if (b->kind != MCG_G_TABLE || !b->faces || b->nu < 2 || b->nv < 2)
+        return set_error(MCG_ERR_ARG, "table_pack needs tables with nu, nv >= 2");
+    if ((uintptr_t)out % 16 != 0) return set_error(MCG_ERR_ARG, "packed tables must be 16-byte aligned");
+    const int64_t n = 6ll * (b->nu - 1) * (b->nv - 1);
+    if (n >= 2147483647LL) return set_error(MCG_ERR_ARG, "tables too large to pack");
+    table_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b->faces, b->nu, b->nv, (float4*)out);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MCG_OK : set_error(MCG_ERR_CUDA, "table pack kernel: %s", cudaGetErrorString(e));
+}
 
 int grf_density(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, double sigma_vox, double amp, float* grid_out,
                 double* work, cudaStream_t st)

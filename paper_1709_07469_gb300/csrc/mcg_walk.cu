@@ -38,6 +38,9 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kNaN = __builtin_nan("");
 
+__device__ __forceinline__ double no_record() { return __longlong_as_double(kNoRecordBits); }
+__device__ __forceinline__ bool has_record(double d) { return __double_as_longlong(d) != kNoRecordBits; }
+
 // Claims new items for the lanes of this warp that are free.  Returns the
 // claimed item in `item`; lanes beyond the end of the work list become
 // `exhausted`.
@@ -78,7 +81,7 @@ __device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsi
         P.pp_u[item] = kNaN;
         P.pp_d[item] = kNaN;
         P.pp_steps[item] = 0;
-        if (P.drec) P.drec[item] = kNaN;  // the exit kernel then writes NaN too
+        if (P.drec) P.drec[item] = no_record();  // the exit kernel then writes NaN too
         atomicOr(P.status, 1 << MCG_ERR_ARG);
     }
     return ok;
@@ -426,7 +429,12 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 
     for (;;) {
         if ((++iter & 255u) == 0u && cancelled(P)) {
-            if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
+            if ((threadIdx.x & 31) == 0) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
+            if (busy) {  // this walk gives no result
+                P.pp_u[item] = kNaN;
+                P.pp_d[item] = kNaN;
+                P.pp_steps[item] = steps;
+            }
             busy = false;
             exhausted = true;
         }
@@ -542,7 +550,13 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
 
     for (;;) {
         if ((++round & 15u) == 0u && cancelled(P)) {
-            if (busy) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
+            // walks in flight, pooled walks and unclaimed items give no result
+            if (lane == 0) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
+            if (busy) {
+                const unsigned long long it = sh_item[t];
+                P.drec[it] = no_record();
+                P.pp_steps[it] = sh_steps[t] + (long long)__popc(alive) * 4 * (long long)blk;
+            }
             busy = false;
             exhausted = true;
             stop = true;
@@ -652,7 +666,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                 // normals are, so all twelve density loads are issued here
                 // and their latency overlaps the steps (same positions, same
                 // summation order: results are unchanged).
-                constexpr bool kPrefetch = RHO == MCG_RHO_VOXEL;
+                constexpr bool kPrefetch = RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked;
                 float px[4], py[4], pz[4], rv[4][3];
                 if constexpr (kPrefetch) {
                     float x = wx, y = wy, zz = wz;
@@ -685,7 +699,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     } else if constexpr (RHO == MCG_RHO_SPHERE) {
                         const float dx = nx - P.sc_f[0], dy = ny - P.sc_f[1], dz = nz - P.sc_f[2];
                         no_rho = dx * dx + dy * dy + dz * dz > P.far_r2;
-                    } else if constexpr (RHO == MCG_RHO_VOXEL) {
+                    } else if constexpr (RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked) {
                         no_rho = false;
                     }
                     if (!(inside_all && no_rho)) {  // otherwise rho = 0 at every copy: sums unchanged
@@ -764,7 +778,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                 } else if (4 * (int64_t)blk >= P.max_steps) {
                     const unsigned long long it = sh_item[t];
                     atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
-                    P.drec[it] = kNaN;  // copy 0 record marks "no result"
+                    P.drec[it] = no_record();  // copy 0 record marks "no result"
                     P.pp_steps[it] = sh_steps[t] + (long long)__popc(alive) * 4 * (long long)blk;
                     busy = false;
                 }
@@ -808,9 +822,10 @@ __device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long lon
 }
 
 // Exit evaluation, convergent: each warp scans its items 32 at a time, writes
-// NaN for the ones without a result (capped, cancelled, outside Omega) and
-// queues the others in shared memory, evaluating them 32 at a time, so the
-// slow double-precision pipe never runs a warp whose lanes are mostly idle.
+// NaN for the ones without a result (a copy without an exit record: capped,
+// cancelled, never started, lost, outside Omega) and queues the others in
+// shared memory, evaluating them 32 at a time, so the slow double-precision
+// pipe never runs a warp whose lanes are mostly idle.
 template <int RHO>
 __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
 {
@@ -824,7 +839,9 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
     for (unsigned long long base = first; base < P.total; base += warps * 32ull) {
         const unsigned long long item = base + (unsigned long long)lane;
         const bool in = item < P.total;
-        const bool valid = in && !isnan(P.drec[item]);
+        bool valid = in && has_record(P.drec[item]);
+        if (P.crn && valid)
+            valid = has_record(P.drec[P.total + item]) && has_record(P.drec[2 * P.total + item]);
         if (in && !valid) {
             P.pp_u[item] = kNaN;
             P.pp_d[item] = kNaN;
@@ -884,6 +901,7 @@ const void* kernel_fn(int precision, int rho_kind, bool crn)
 {
     if (precision == MCG_FP64) return crn ? (const void*)walk_fp64_kernel<true> : (const void*)walk_fp64_kernel<false>;
     switch (rho_kind) {
+    case kRhoVoxelPacked: return mixed_fn<kRhoVoxelPacked>(crn);
     case MCG_RHO_SPHERE: return mixed_fn<MCG_RHO_SPHERE>(crn);
     case MCG_RHO_PRISM: return mixed_fn<MCG_RHO_PRISM>(crn);
     case MCG_RHO_VOXEL: return mixed_fn<MCG_RHO_VOXEL>(crn);
@@ -923,10 +941,12 @@ void preload_walk_kernels()
     touch(exit_mixed_kernel<MCG_RHO_SPHERE>);
     touch(exit_mixed_kernel<MCG_RHO_PRISM>);
     touch(exit_mixed_kernel<MCG_RHO_VOXEL>);
+    touch(exit_mixed_kernel<kRhoVoxelPacked>);
     touch_mixed<MCG_RHO_NONE>();
     touch_mixed<MCG_RHO_SPHERE>();
     touch_mixed<MCG_RHO_PRISM>();
     touch_mixed<MCG_RHO_VOXEL>();
+    touch_mixed<kRhoVoxelPacked>();
 }
 
 int walk_blocks_per_sm(int precision, int rho_kind, int block)
@@ -943,7 +963,8 @@ cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStrea
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = walk_blocks_per_sm(precision, P.rho_kind, block);
+    const int kind = (P.rho_kind == MCG_RHO_VOXEL && P.zq) ? kRhoVoxelPacked : P.rho_kind;
+    const int per_sm = walk_blocks_per_sm(precision, kind, block);
     long long grid = (long long)sms * per_sm;
     const long long need = (long long)((P.total + (unsigned long long)block - 1ull) / (unsigned long long)block);
     if (grid > need) grid = need > 0 ? need : 1;
@@ -953,7 +974,8 @@ cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStrea
         else walk_fp64_kernel<false><<<(int)grid, block, 0, st>>>(P);
         return cudaGetLastError();
     }
-    switch (P.rho_kind) {
+    switch (kind) {
+    case kRhoVoxelPacked: return launch_mixed_rho<kRhoVoxelPacked>(P, block, (int)grid, st);
     case MCG_RHO_SPHERE: return launch_mixed_rho<MCG_RHO_SPHERE>(P, block, (int)grid, st);
     case MCG_RHO_PRISM: return launch_mixed_rho<MCG_RHO_PRISM>(P, block, (int)grid, st);
     case MCG_RHO_VOXEL: return launch_mixed_rho<MCG_RHO_VOXEL>(P, block, (int)grid, st);

@@ -13,9 +13,26 @@ import torch
 from . import mcgrav as M
 
 
+def packed(w, grid, faces, stream=None):
+    """Packed copies of a device voxel grid and device boundary tables for the
+    walk's 16-byte loads (mcg_voxel_pack / mcg_table_pack): (zpack, quads),
+    None where the workload has no such array or the packed grid does not
+    apply (h > half a cell height)."""
+    zpack = quads = None
+    if grid is not None and w.rho_kind == "voxel" and grid.is_cuda and w.h <= 0.5 * w.grid_spacing[2]:
+        nz, ny, nx = grid.shape
+        zpack = torch.empty(M.mcg_voxel_pack_bytes(nx, ny, nz) // 4, dtype=torch.float32, device=grid.device)
+        M.mcg_voxel_pack(M.problem(w.with_(g_kind="zero"), grid=grid), zpack, stream)
+    if faces is not None and w.g_kind == "table" and faces.is_cuda:
+        quads = torch.empty(M.mcg_table_pack_bytes(faces.shape[2], faces.shape[1]) // 4, dtype=torch.float32,
+                            device=faces.device)
+        M.mcg_table_pack(M.problem(w.with_(rho_kind="none"), faces=faces), quads, stream)
+    return zpack, quads
+
+
 class DeviceSolve:
     def __init__(self, w, stations=None, batch: int | None = None, precision: int = M.MCG_MIXED,
-                 grid=None, faces=None, device: str = "cuda", stream=None, block: int = 0):
+                 grid=None, faces=None, device: str = "cuda", stream=None, block: int = 0, pack: bool = True):
         self.w = w
         self.dev = torch.device(device)
         st = np.asarray(w.stations if stations is None else stations, dtype=np.float64).reshape(-1, 3)
@@ -24,7 +41,8 @@ class DeviceSolve:
         self.batch = int(batch or w.paths)
         self.precision = precision
         self.stream = stream
-        self.prob = M.problem(w, grid=grid, faces=faces)
+        zpack, quads = packed(w, grid, faces, stream) if pack else (None, None)
+        self.prob = M.problem(w, grid=grid, faces=faces, zpack=zpack, quads=quads)
         self.opts = M.options(w, precision=precision, stream=stream, block=block)
         n = self.S * self.batch
         self.pp_u = torch.empty(n, dtype=torch.float64, device=self.dev)

@@ -35,12 +35,13 @@ class mcg_domain(C.Structure):
 class mcg_density(C.Structure):
     _fields_ = [("kind", C.c_int32), ("G", C.c_double), ("rho0", C.c_double), ("center", D3),
                 ("radius", C.c_double), ("lo", D3), ("hi", D3), ("grid", C.c_void_p),
-                ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("origin", D3), ("spacing", D3)]
+                ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("origin", D3), ("spacing", D3),
+                ("zpack", C.c_void_p)]
 
 
 class mcg_boundary(C.Structure):
     _fields_ = [("kind", C.c_int32), ("faces", C.c_void_p), ("nu", C.c_int32), ("nv", C.c_int32),
-                ("poly", C.c_double * 11)]
+                ("poly", C.c_double * 11), ("quads", C.c_void_p)]
 
 
 class mcg_options(C.Structure):
@@ -48,7 +49,7 @@ class mcg_options(C.Structure):
                 ("crn_gz", C.c_int32), ("block", C.c_int32), ("max_steps", C.c_int64),
                 ("batch_paths", C.c_int64), ("stream", C.c_void_p), ("cancel", C.c_void_p),
                 ("bridge", C.c_int32), ("refill_min", C.c_int32), ("graph", C.c_int32),
-                ("migrate", C.c_int32)]
+                ("migrate", C.c_int32), ("fault_unpublished", C.c_int32)]
 
 
 class mcg_result(C.Structure):
@@ -151,6 +152,18 @@ def load(path: str | None = None):
     lib.mcg_finalize.restype = C.c_int
     lib.mcg_workspace_bytes.argtypes = [i64, i64]
     lib.mcg_workspace_bytes.restype = C.c_size_t
+    lib.mcg_voxel_pack_bytes.argtypes = [i64, i64, i64]
+    lib.mcg_voxel_pack_bytes.restype = C.c_size_t
+    lib.mcg_voxel_pack.argtypes = [P(mcg_density), vp, vp]
+    lib.mcg_voxel_pack.restype = C.c_int
+    lib.mcg_table_pack_bytes.argtypes = [i32, i32]
+    lib.mcg_table_pack_bytes.restype = C.c_size_t
+    lib.mcg_table_pack.argtypes = [P(mcg_boundary), vp, vp]
+    lib.mcg_table_pack.restype = C.c_int
+    lib.mcg_issue_probe.argtypes = [i32, i32, P(d), P(d)]
+    lib.mcg_issue_probe.restype = C.c_int
+    lib.mcg_field.argtypes = [P(mcg_density), vp, i64, vp, vp, vp]
+    lib.mcg_field.restype = C.c_int
     lib.mcg_philox.argtypes = [vp, vp, i64, vp, vp]
     lib.mcg_philox.restype = C.c_int
     lib.mcg_normals.argtypes = [u64, u32, u32, u32, i64, i32, vp, vp]
@@ -202,9 +215,11 @@ class Problem:
     keep: tuple = ()
 
 
-def problem(w, grid=None, faces=None) -> Problem:
+def problem(w, grid=None, faces=None, zpack=None, quads=None) -> Problem:
     """C structures of a workload (paper_1709_07469_gb300.workloads.Workload).
-    `grid` / `faces` are device tensors (float32) when the workload uses them."""
+    `grid` / `faces` are device tensors (float32) when the workload uses them;
+    `zpack` / `quads` their optional packed copies (mcg_voxel_pack /
+    mcg_table_pack, device tensors)."""
     dom = mcg_domain(D3(*w.lo), D3(*w.hi), 1 if getattr(w, "domain", "box") == "ball" else 0,
                      D3(*getattr(w, "ball_center", (0.0, 0.0, 0.0))), getattr(w, "ball_radius", 0.0))
     den = mcg_density()
@@ -220,6 +235,7 @@ def problem(w, grid=None, faces=None) -> Problem:
         den.grid = _ptr(grid)
         den.nx, den.ny, den.nz = nx, ny, nz
         den.origin, den.spacing = D3(*w.grid_origin), D3(*w.grid_spacing)
+        den.zpack = _ptr(zpack)
     bnd = mcg_boundary()
     bnd.kind = _G[w.g_kind]
     bnd.poly = (C.c_double * 11)(*[float(c) for c in w.poly])
@@ -228,7 +244,8 @@ def problem(w, grid=None, faces=None) -> Problem:
             raise ValueError("table workload needs device faces")
         bnd.faces = _ptr(faces)
         bnd.nv, bnd.nu = faces.shape[1], faces.shape[2]
-    return Problem(dom, den, bnd, (grid, faces))
+        bnd.quads = _ptr(quads)
+    return Problem(dom, den, bnd, (grid, faces, zpack, quads))
 
 
 def options(w=None, precision: int = MCG_MIXED, stream=None, **kw) -> mcg_options:
@@ -335,6 +352,35 @@ def mcg_grf_density(seed: int, nx: int, ny: int, nz: int, sigma_vox: float, amp:
 def mcg_boundary_tables(prob: Problem, nu: int, nv: int, near_cells: float, faces_out, stream=None) -> int:
     return _check(load().mcg_boundary_tables(C.byref(prob.domain), C.byref(prob.density), nu, nv, near_cells,
                                              _ptr(faces_out), _stream_handle(stream)))
+
+
+def mcg_issue_probe(kind: int, iters: int = 4096):
+    """(lane-instructions per second, seconds) of the issue-rate probe."""
+    rate, secs = C.c_double(), C.c_double()
+    _check(load().mcg_issue_probe(kind, iters, C.byref(rate), C.byref(secs)))
+    return rate.value, secs.value
+
+
+def mcg_voxel_pack_bytes(nx: int, ny: int, nz: int) -> int:
+    return int(load().mcg_voxel_pack_bytes(nx, ny, nz))
+
+
+def mcg_voxel_pack(prob: Problem, out_dev, stream=None) -> int:
+    return _check(load().mcg_voxel_pack(C.byref(prob.density), _ptr(out_dev), _stream_handle(stream)))
+
+
+def mcg_table_pack_bytes(nu: int, nv: int) -> int:
+    return int(load().mcg_table_pack_bytes(nu, nv))
+
+
+def mcg_table_pack(prob: Problem, out_dev, stream=None) -> int:
+    return _check(load().mcg_table_pack(C.byref(prob.boundary), _ptr(out_dev), _stream_handle(stream)))
+
+
+def mcg_field(prob: Problem, points_dev, n: int, phi_dev=None, gz_dev=None, stream=None) -> int:
+    """Exact Phi and dPhi/dz of the problem's density model at n device points."""
+    return _check(load().mcg_field(C.byref(prob.density), _ptr(points_dev), n, _ptr(phi_dev), _ptr(gz_dev),
+                                   _stream_handle(stream)))
 
 
 STATE_FIELDS = ("n", "mean_u", "m2_u", "mean_d", "m2_d", "steps")

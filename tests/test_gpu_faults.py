@@ -3,10 +3,17 @@
 * Cancellation: a device flag that the walk polls, written by an
   asynchronous copy on another stream while a long walk runs: the kernel
   stops taking work, returns promptly and reports MCG_ERR_CANCELLED (no trap,
-  no abandoned wait).  It runs first in a fresh process on purpose: the
+  no abandoned wait); every item that did not finish reads NaN, whatever the
+  scratch held before.  It runs first in a fresh process on purpose: the
   library loads its kernels before the first launch, so queueing the exit
   kernel behind the running walk does not block the host until the walk
   ends (what CUDA's lazy module loading would otherwise do).
+* A bounded wait that runs out: the launch starts with a migration-pool slot
+  reserved and never published (the host-side hook fault_unpublished, a
+  stand-in for a warp that died between reserving and writing).  The warp
+  that claims it waits a bounded time, gives up, and the walk reports
+  MCG_ERR_TIMEOUT through mcg_walk, mcgrav_solve and the server; every real
+  walk is unaffected.  Nothing faults, traps or hangs.
 * Non-finite data (a NaN in the boundary tables) reaches the status word as
   MCG_ERR_NONFINITE; the step cap as MCG_ERR_STEP_CAP.
 * Checkpoint / resume: station states (64 bytes each) saved after half the
@@ -40,7 +47,12 @@ def _long_walk(cancel_ptr, stream=None):
     ds = DeviceSolve(w, batch=65536, precision=M.MCG_MIXED, stream=stream)   # ~2 s of work uncancelled
     ds.opts.cancel = cancel_ptr
     ds.reset()
-    ds.work.fill_(255)          # stale records would read as NaN, not as results
+    # scratch and outputs hold finite leftovers (zero exit records would read
+    # as valid results if the walk did not mark its items first)
+    ds.work.zero_()
+    ds.pp_u.zero_()
+    ds.pp_d.zero_()
+    ds.pp_steps.fill_(7)
     torch.cuda.synchronize()
     return ds
 
@@ -59,6 +71,58 @@ def test_cancel_flag_in_device_memory_set_by_a_copy():
     elapsed = time.perf_counter() - t0
     assert int(ds.status[0].item()) & (1 << M.MCG_ERR_CANCELLED), elapsed
     assert elapsed < 1.0
+    u, d, steps = ds.per_path()
+    unfinished = np.isnan(u)
+    assert unfinished.mean() > 0.5                       # cancelled after ~10 % of the work
+    assert np.isnan(d[unfinished]).all()
+    assert np.isfinite(u[~unfinished]).all() and np.isfinite(d[~unfinished]).all()
+    assert (steps[~unfinished] > 0).all()
+    assert (steps != 7).all()                            # every item's steps written by this launch
+    assert (steps == 0).sum() > 0                        # items never started
+
+
+def _timeout_opts(w, **kw):
+    return M.options(w, precision=M.MCG_MIXED, fault_unpublished=1, **kw)
+
+
+def test_bounded_pool_wait_gives_up_with_timeout():
+    w = W.sphere_line(paths=4096)
+    ref = DeviceSolve(w, precision=M.MCG_MIXED)
+    ref.reset()
+    ref.walk(0)
+    u0, d0, s0 = ref.per_path()
+    assert int(ref.status[0].item()) == 0
+    ds = DeviceSolve(w, precision=M.MCG_MIXED)
+    ds.opts.fault_unpublished = 1
+    ds.reset()
+    t0 = time.perf_counter()
+    ds.walk(0)
+    u, d, s = ds.per_path()
+    elapsed = time.perf_counter() - t0
+    assert int(ds.status[0].item()) == 1 << M.MCG_ERR_TIMEOUT
+    assert elapsed < 10.0
+    # the reserved slot held no walk: every real walk finished unchanged
+    assert np.array_equal(s, s0)
+    assert np.array_equal(u, u0) and np.array_equal(d, d0)
+
+
+def test_timeout_reaches_the_solver_and_the_server():
+    w = W.sphere_line(paths=2048)
+    r = M.mcgrav_solve(M.problem(w), w.stations, 2048, w.dt, 0, _timeout_opts(w), allow=(M.MCG_ERR_TIMEOUT,))
+    assert r.status == M.MCG_ERR_TIMEOUT
+    assert "bounded wait" in M.last_error()
+    model = M.mcg_model_create(M.problem(w), w.dt, w.h)
+    sv = M.mcg_server_create(M.server_config(_timeout_opts(w), chunk_paths=1024, min_paths=1024))
+    try:
+        rq = M.mcg_submit(sv, model, w.stations[:3], 1e-2, 5)
+        M.mcg_wait(rq, 3, 60_000)
+        done, rc, _ = M.mcg_poll(rq, 3)
+        assert done == 1
+        M.mcg_request_free(rq)
+    finally:
+        M.mcg_server_destroy(sv)
+        M.mcg_model_destroy(model)
+    assert rc == M.MCG_ERR_TIMEOUT      # never finished as a success
 
 
 def test_nonfinite_boundary_data_is_reported():

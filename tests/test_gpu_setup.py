@@ -23,7 +23,7 @@ import oracle
 from paper_1709_07469_gb300 import build as B
 from paper_1709_07469_gb300 import mcgrav as M
 from paper_1709_07469_gb300 import workloads as W
-from paper_1709_07469_gb300.device import DeviceSolve, voxel_model
+from paper_1709_07469_gb300.device import DeviceSolve, packed, voxel_model
 from tests.helpers import oracle_spec, smooth_tables
 
 pytestmark = pytest.mark.gpu
@@ -209,3 +209,52 @@ def test_mcgrav_solve_takes_host_or_device_model_arrays(voxel_inputs):
         assert np.array_equal(getattr(host, k), getattr(dev, k)), k
     for k in ("u", "gz", "se_u", "se_gz"):
         np.testing.assert_allclose(getattr(host, k), getattr(dev, k), rtol=1e-5, err_msg=k)
+
+
+def test_packed_arrays_layout(voxel_inputs):
+    """mcg_voxel_pack: entry (iz + 1, iy, ix) holds layers iz-1, iz, iz+1 of
+    the column (0 outside the grid); mcg_table_pack: entry (f, iv, iu) holds
+    the four corners of that table cell."""
+    w, grid, faces = voxel_inputs
+    nz, ny, nx = grid.shape
+    zp, tq = packed(w, torch.from_numpy(grid).cuda(), torch.from_numpy(faces).cuda())
+    torch.cuda.synchronize()
+    zp = zp.cpu().numpy().reshape(nz + 2, ny, nx, 4)
+    pad = np.zeros((nz + 4, ny, nx), dtype=np.float32)
+    pad[2:nz + 2] = grid
+    for d in range(3):
+        assert np.array_equal(zp[..., d], pad[d:d + nz + 2])
+    assert np.all(zp[..., 3] == 0)
+    nv, nu = faces.shape[1:]
+    tq = tq.cpu().numpy().reshape(6, nv - 1, nu - 1, 4)
+    assert np.array_equal(tq[..., 0], faces[:, :-1, :-1]) and np.array_equal(tq[..., 1], faces[:, :-1, 1:])
+    assert np.array_equal(tq[..., 2], faces[:, 1:, :-1]) and np.array_equal(tq[..., 3], faces[:, 1:, 1:])
+
+
+def test_packed_walks_read_the_same_values(voxel_inputs):
+    """The 16-byte packed reads give the walk the same densities and table
+    values as the scalar reads: the FP64 walk (packed tables) is bit-identical
+    path by path; the mixed walk (packed grid and tables) has identical exit
+    steps and u, d equal up to the schedule-dependent flush rounding of its
+    single-precision partial sums (4e-6 of max |u|, as with migration)."""
+    w, grid, faces = voxel_inputs
+    g, f = torch.from_numpy(grid).cuda(), torch.from_numpy(faces).cuda()
+    wg = w.with_(stations=w.stations[[2, 90, 171, 240]], paths=2048)
+    out = {}
+    for prec in (M.MCG_FP64, M.MCG_MIXED):
+        for pack in (True, False):
+            n = 64 if prec == M.MCG_FP64 else 2048
+            ds = DeviceSolve(wg, batch=n, precision=prec, grid=g, faces=f, pack=pack)
+            assert (ds.prob.density.zpack is not None) == pack
+            ds.reset()
+            ds.walk(0)
+            out[prec, pack] = ds.per_path() + (int(ds.status[0].item()),)
+    a, b = out[M.MCG_FP64, True], out[M.MCG_FP64, False]
+    assert a[3] == 0 and b[3] == 0
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    a, b = out[M.MCG_MIXED, True], out[M.MCG_MIXED, False]
+    assert a[3] == 0 and b[3] == 0
+    assert np.array_equal(a[2], b[2])
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=4e-6 * np.abs(b[0]).max())
+    np.testing.assert_allclose(a[1], b[1], rtol=0, atol=4e-6 * np.abs(b[0]).max() / w.h)
