@@ -62,6 +62,23 @@ def worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
+def bench_worker(rank, world, port, q):
+    """The benchmark's own exchange step (bench.merge_rank_states), on gloo."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        M.load()
+        u, d, steps = per_path_values()
+        blocks = [b for b in range(N_PATHS // BLOCK) if b % world == rank]
+        cols = np.concatenate([np.arange(b * BLOCK, (b + 1) * BLOCK) for b in blocks])
+        mine = torch.from_numpy(state_of(u[:, cols], d[:, cols], steps[:, cols]).reshape(-1).copy())
+        merged = bench.merge_rank_states(M, mine, S, world)
+        q.put((rank, merged.numpy().reshape(S, 8)))
+    finally:
+        dist.destroy_process_group()
+
+
 def free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -102,3 +119,27 @@ def test_merge_rank_order_and_empty_parts():
     got = M.mcg_states_merge(parts)
     ref = state_of(x, x, np.ones((3, 900)))
     np.testing.assert_allclose(got[:, :6], ref[:, :6], rtol=1e-12)
+
+
+def test_bench_exchange_step_on_gloo():
+    """bench.py's N > 1 branch merges the ranks' station states with this
+    function; on two gloo ranks it gives every rank the single-process
+    statistics of all paths."""
+    B.build()
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=bench_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    u, d, steps = per_path_values()
+    ref = state_of(u, d, steps)
+    assert np.array_equal(results[0], results[1])
+    assert np.array_equal(results[0][:, 0], ref[:, 0])
+    np.testing.assert_allclose(results[0][:, [1, 3]], ref[:, [1, 3]], rtol=1e-13)
+    np.testing.assert_allclose(results[0][:, [2, 4]], ref[:, [2, 4]], rtol=1e-11)
