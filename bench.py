@@ -712,7 +712,8 @@ def run_serving(args):
 def large_survey_block(M, W, steps, warmup, paths):
     """Large survey: 2 x 10^4 stations (surface + airborne grids) over the
     GPU-built voxel model, mixed precision, one autotuned persistent launch
-    per step; stations/s at 1e-3 relative SE from the measured per-path
+    per step, steps alternating between two streams; stations/s at 1e-3
+    relative SE from the measured per-path
     spread, against the plain FP64 walk at equal standard error; error of
     256 sampled stations against the exact field of the voxel model
     (mcg_field: the voxels' prism sums regrouped by grid node)."""
@@ -726,24 +727,47 @@ def large_survey_block(M, W, steps, warmup, paths):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     N = paths
-    ds = DeviceSolve(w, batch=N, precision=M.MCG_MIXED, grid=grid, faces=faces)
+    # consecutive steps alternate between two streams (one step's exit-time
+    # tail runs beside the next step); the reductions into the one set of
+    # station states are chained by events, so they merge in step order
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pair = [DeviceSolve(w, batch=N, precision=M.MCG_MIXED, grid=grid, faces=faces, stream=s) for s in streams]
+    ds = pair[0]
     M.mcg_autotune(ds.prob, ds.stations, ds.S, w.dt, w.seed, ds.opts)
+    pair[1].opts.block, pair[1].opts.refill_min = ds.opts.block, ds.opts.refill_min
+    pair[1].states = ds.states
+
+    def run_steps(first, count):
+        prev = None
+        for j in range(first, first + count):
+            d, s = pair[j % 2], streams[j % 2]
+            d.walk(j * N)
+            if prev is not None:
+                s.wait_event(prev)
+            d.reduce()
+            prev = torch.cuda.Event()
+            prev.record(s)
+        return prev
+
     ds.reset()
-    for j in range(warmup):
-        ds.walk(j * N)
-        ds.reduce()
+    pair[1].status.zero_()
+    torch.cuda.synchronize()   # the resets run on the default stream
+    run_steps(0, warmup)
     torch.cuda.synchronize()
     ds.reset()
+    pair[1].status.zero_()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for j in range(steps):
-        ds.walk((warmup + j) * N)
-        ds.reduce()
+    e0.record(streams[0])
+    streams[1].wait_event(e0)
+    last = run_steps(warmup, steps)
+    streams[0].wait_event(last)
     ds.finalize()
-    e1.record()
+    e1.record(streams[0])
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     r = ds.result()
+    r["status"] |= int(pair[1].status[0].item())
     steps_total = float(r["path_steps"].sum())
     n = r["n_paths"].astype(np.float64)
     s_u = r["se_u"] * np.sqrt(n)
