@@ -644,12 +644,13 @@ def serving_block(M, W, args):
     targets = rng.choice([1e-2, 3e-3, 1e-3], n)
     mk = rng.integers(0, 16, n)
     st_idx = [rng.choice(base.n_stations, size=int(s), replace=False) for s in S]
-    cfg = M.server_config(M.options(base, precision=M.MCG_MIXED, migrate=args.migrate), chunk_paths=4096,
-                          min_paths=8192, hbm_budget=16 << 30, streams=args.serve_streams, max_active=64,
-                          max_round_paths=args.max_round_paths)
+    def config(batch):
+        return M.server_config(M.options(base, precision=M.MCG_MIXED, migrate=args.migrate), chunk_paths=4096,
+                               min_paths=8192, hbm_budget=16 << 30, streams=args.serve_streams, max_active=64,
+                               max_round_paths=args.max_round_paths, batch=batch)
 
-    def replay(arrivals):
-        sv = M.mcg_server_create(cfg)
+    def replay(arrivals, batch=1):
+        sv = M.mcg_server_create(config(batch))
         reqs = [None] * n
         t_start = time.perf_counter()
         i = 0
@@ -672,11 +673,15 @@ def serving_block(M, W, args):
                     outstanding.discard(j)
             time.sleep(0.0005)
         makespan = time.perf_counter() - t_start
+        launches, rounds = M.mcg_server_stats(sv)
         M.mcg_server_destroy(sv)
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "stations_per_s": stations_done / makespan, "path_steps_per_s": path_steps / makespan,
-                "makespan_s": makespan, "offered_span_s": float(arrivals[-1])}
+                "makespan_s": makespan, "offered_span_s": float(arrivals[-1]),
+                "walk_launches": launches, "rounds": rounds}
 
+    # every round in a launch of its own, for comparison with the shared launches
+    alone = replay(np.zeros(n), batch=0)
     closed = replay(np.zeros(n))
     capacity = n / closed["makespan_s"]
     levels = [("closed (all at t = 0)", None, closed)]
@@ -689,11 +694,14 @@ def serving_block(M, W, args):
     for m in models:
         M.mcg_model_destroy(m)
     return {"requests": n, "capacity_requests_per_s": capacity,
+            "capacity_one_launch_per_round": {"requests_per_s": n / alone["makespan_s"],
+                                              "p50_ms": alone["p50_ms"], "p99_ms": alone["p99_ms"]},
             "levels": [dict(load=name, rate_per_s=rate, **r) for name, rate, r in levels],
             "model_setup_s": setup_s,
             "config": {"workload": "voxel_survey x 16 models (seeds 0-15)", "stations_per_request": "U{1..64}",
                        "targets": [1e-2, 3e-3, 1e-3], "chunk_paths": 4096, "streams": args.serve_streams,
-                       "max_round_paths": args.max_round_paths, "hbm_budget_gib": 16}}
+                       "max_round_paths": args.max_round_paths, "hbm_budget_gib": 16,
+                       "shared_launches": "rounds of compatible requests share walk launches (batch = 1)"}}
 
 
 def run_serving(args):

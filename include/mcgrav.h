@@ -383,7 +383,7 @@ typedef struct mcg_server mcg_server;
 typedef struct mcg_request mcg_request;
 
 typedef struct {
-    int32_t streams;          /* stream pool size (default 8)                       */
+    int32_t streams;          /* stream slots, one launch in flight on each (default 8) */
     int32_t max_active;       /* requests in flight at most (default 64)             */
     int64_t hbm_budget;       /* bytes of request buffers in flight (default 8 GiB)  */
     int64_t chunk_paths;      /* paths per station per round (default 4096)          */
@@ -393,6 +393,14 @@ typedef struct {
                                  after min_paths the next round walks the chunks the
                                  request's own spread says it still needs, in one launch */
     mcg_options walk;         /* walk options (precision, h, sigma, clip, crn_gz, block, max_steps) */
+    int32_t batch;            /* 1 (default): ready rounds of requests whose problems share
+                                 every scalar (domain, density and boundary kinds, grid
+                                 geometry, dt, h) share one walk launch, each request a
+                                 segment with its own stations, seed and model arrays;
+                                 0: one walk launch per round.  Box domain without the
+                                 bridge test; other requests always run alone.    */
+    int64_t batch_items;      /* walks in one shared launch at most (default 2^22); the
+                                 ready rounds are spread over the free stream slots  */
 } mcg_server_config;
 
 MCG_API void mcg_server_config_default(mcg_server_config* c);
@@ -432,6 +440,10 @@ MCG_API int mcg_cancel(mcg_request* r);
  * submit to completion (or so far).  Any pointer may be NULL. */
 MCG_API int mcg_request_info(const mcg_request* r, int64_t* paths, int64_t* rounds, double* seconds);
 MCG_API int mcg_request_free(mcg_request* r);
+/* mcg_server_stats: walk launches so far and the request rounds they ran
+ * (rounds / launches = requests per shared launch).  Either pointer may be
+ * NULL. */
+MCG_API int mcg_server_stats(const mcg_server* s, int64_t* launches, int64_t* rounds);
 
 /* ---------------------------------------------------------------------- */
 /* Heterogeneous model set-up (once per model, outside the walk).            */

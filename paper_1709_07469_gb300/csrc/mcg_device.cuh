@@ -127,6 +127,36 @@ __device__ __forceinline__ void normals12_f32(uint32_t s, uint32_t p, uint32_t b
 }
 
 // ---------------------------------------------------------------------------
+// The model arrays a walk reads: the launch's own, or (multi-request launch)
+// those of the walk's request.
+// ---------------------------------------------------------------------------
+struct ModelRef {
+    const float* grid;
+    const float4* zq;
+    const float* faces;
+    const float4* tq;
+};
+
+__device__ __forceinline__ ModelRef model_of(const WalkParams& P) { return ModelRef{P.grid, P.zq, P.faces, P.tq}; }
+
+__device__ __forceinline__ ModelRef model_of(const WalkSeg& g)
+{
+    return ModelRef{g.grid, g.zq, g.faces, g.tq};
+}
+
+// Segment of launch item `item` (binary search over the sorted begins).
+__device__ __forceinline__ int find_seg(const WalkParams& P, unsigned long long item)
+{
+    int lo = 0, hi = P.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&P.seg[mid].begin) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
 // Density samplers.
 // ---------------------------------------------------------------------------
 // Density at the three common-random-number copies (x, y, z), (x, y, z+h),
@@ -135,8 +165,8 @@ __device__ __forceinline__ void normals12_f32(uint32_t s, uint32_t p, uint32_t b
 // exit kernel, which re-evaluates rho at the last inside point, agree bit for
 // bit.
 template <int RHO>
-__device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, float z, float h, float& ra,
-                                         float& rb, float& rc)
+__device__ __forceinline__ void rho3_f32(const WalkParams& P, const ModelRef& M, float x, float y, float z, float h,
+                                         float& ra, float& rb, float& rc)
 {
     if constexpr (RHO == MCG_RHO_SPHERE) {
         const float dx = __fsub_rn(x, P.sc_f[0]), dy = __fsub_rn(y, P.sc_f[1]), dz = __fsub_rn(z, P.sc_f[2]);
@@ -160,9 +190,9 @@ __device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, 
         const float zb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
         const float zc = floorf(__fmul_rn(__fsub_rn(__fsub_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
         const int plane = P.nx * P.ny;
-        ra = (inxy && za >= 0.f && za < (float)P.nz) ? __ldg(P.grid + base + plane * (int)za) : 0.0f;
-        rb = (inxy && zb >= 0.f && zb < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zb) : 0.0f;
-        rc = (inxy && zc >= 0.f && zc < (float)P.nz) ? __ldg(P.grid + base + plane * (int)zc) : 0.0f;
+        ra = (inxy && za >= 0.f && za < (float)P.nz) ? __ldg(M.grid + base + plane * (int)za) : 0.0f;
+        rb = (inxy && zb >= 0.f && zb < (float)P.nz) ? __ldg(M.grid + base + plane * (int)zb) : 0.0f;
+        rc = (inxy && zc >= 0.f && zc < (float)P.nz) ? __ldg(M.grid + base + plane * (int)zc) : 0.0f;
     } else if constexpr (RHO == kRhoVoxelPacked) {
         // The same cells as above, read through the packed grid: the copies'
         // layers zb, zc differ from za by at most one (h <= half a cell), and
@@ -176,7 +206,7 @@ __device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, 
         const bool in = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny && za >= -1.f &&
                         za <= (float)P.nz;
         float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in) q = __ldg(P.zq + ((int)za + 1) * P.ny * P.nx + (int)ty * P.nx + (int)tx);
+        if (in) q = __ldg(M.zq + ((int)za + 1) * P.ny * P.nx + (int)ty * P.nx + (int)tx);
         ra = q.y;
         rb = zb > za ? q.z : q.y;
         rc = zc < za ? q.x : q.y;
@@ -186,7 +216,7 @@ __device__ __forceinline__ void rho3_f32(const WalkParams& P, float x, float y, 
 }
 
 // Double precision density at an absolute point (same cells as above).
-__device__ __forceinline__ double rho_f64(const WalkParams& P, const double x[3])
+__device__ __forceinline__ double rho_f64(const WalkParams& P, const ModelRef& M, const double x[3])
 {
     switch (P.rho_kind) {
     case MCG_RHO_SPHERE: {
@@ -207,7 +237,7 @@ __device__ __forceinline__ double rho_f64(const WalkParams& P, const double x[3]
             if (!(t >= 0.0 && t < (double)n[k])) return 0.0;
             idx[k] = (int)t;
         }
-        return (double)__ldg(P.grid + idx[0] + P.nx * (idx[1] + P.ny * idx[2]));
+        return (double)__ldg(M.grid + idx[0] + P.nx * (idx[1] + P.ny * idx[2]));
     }
     default:
         return 0.0;
@@ -266,11 +296,11 @@ __device__ __forceinline__ double sphere_potential(const WalkParams& P, const do
 }
 
 // Bilinear read of face `face` (0..5) at the absolute boundary point x.
-__device__ __forceinline__ double table_value(const WalkParams& P, int face, const double x[3])
+__device__ __forceinline__ double table_value(const WalkParams& P, const ModelRef& M, int face, const double x[3])
 {
     const int k = face >> 1;
     const int a = (k == 0) ? 1 : 0, b = (k == 2) ? 1 : 2;
-    const float* t = P.faces + (int64_t)face * P.nu * P.nv;
+    const float* t = M.faces + (int64_t)face * P.nu * P.nv;
     const double tu = (x[a] - P.lo[a]) / (P.hi[a] - P.lo[a]) * (double)(P.nu - 1);
     const double tv = (x[b] - P.lo[b]) / (P.hi[b] - P.lo[b]) * (double)(P.nv - 1);
     const double fu = fmin(fmax(floor(tu), 0.0), (double)(P.nu - 2));
@@ -278,8 +308,8 @@ __device__ __forceinline__ double table_value(const WalkParams& P, int face, con
     const int iu = (int)fu, iv = (int)fv;
     const double au = tu - fu, av = tv - fv;
     double f00, f10, f01, f11;
-    if (P.tq) {  // the cell's four corners in one 16-byte load
-        const float4 c = __ldg(P.tq + ((int64_t)face * (P.nv - 1) + iv) * (P.nu - 1) + iu);
+    if (M.tq) {  // the cell's four corners in one 16-byte load
+        const float4 c = __ldg(M.tq + ((int64_t)face * (P.nv - 1) + iv) * (P.nu - 1) + iu);
         f00 = c.x;
         f10 = c.y;
         f01 = c.z;
@@ -295,7 +325,7 @@ __device__ __forceinline__ double table_value(const WalkParams& P, int face, con
 }
 
 // g at the absolute exit point x on face `face` (-1 if not on a face).
-static __device__ __noinline__ double boundary_value(const WalkParams& P, int face, const double* x)
+static __device__ __noinline__ double boundary_value(const WalkParams& P, const ModelRef& M, int face, const double* x)
 {
     switch (P.g_kind) {
     case MCG_G_SPHERE:
@@ -303,7 +333,7 @@ static __device__ __noinline__ double boundary_value(const WalkParams& P, int fa
     case MCG_G_PRISM:
         return prism_potential(P.G, P.rho0, P.plo, P.phi, x);
     case MCG_G_TABLE:
-        return face < 0 ? __longlong_as_double(0x7ff8000000000000LL) : table_value(P, face, x);
+        return face < 0 ? __longlong_as_double(0x7ff8000000000000LL) : table_value(P, M, face, x);
     case MCG_G_POLY: {
         const double* c = P.poly;
         const double X = x[0], Y = x[1], Z = x[2];

@@ -70,6 +70,27 @@ struct WalkParams {
     unsigned long long* pool_ctr;
     unsigned long long pool_cap;
     uint32_t fault_unpublished;    // host side: pool slots reserved and never published
+    // multi-request launch: segment table (device) sorted by begin, or null
+    const struct WalkSeg* seg;
+    int32_t nseg;
+};
+
+// One request's part of a multi-request walk launch (the server's batched
+// rounds): items begin .. begin + S N - 1 of the launch are paths p0 .. p0 +
+// N - 1 of each of the request's S stations, item begin + s N + (p - p0).
+// The requests of one launch share every scalar of the problem (domain,
+// density and boundary kinds, grid geometry, step, h) but have their own
+// stations, generator key, status word and model arrays.
+struct WalkSeg {
+    unsigned long long begin;
+    const double* stations;
+    int64_t N, p0;
+    int32_t* status;
+    const float* grid;
+    const float4* zq;
+    const float* faces;
+    const float4* tq;
+    uint32_t key0, key1;
 };
 
 // Exit-record marker of an item without a result (never started, cancelled,
@@ -103,7 +124,7 @@ cudaError_t reset_walk(const WalkParams& P, cudaStream_t st);
 
 // Kernel launchers (mcg_walk.cu).
 cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStream_t st);
-int walk_blocks_per_sm(int precision, int rho_kind, int block);
+int walk_blocks_per_sm(int precision, int rho_kind, int block, bool seg = false);
 
 // Reduction launchers (mcg_reduce.cu).
 cudaError_t launch_reduce(const double* pp_u, const double* pp_d, const int64_t* pp_steps, int64_t S,

@@ -1,15 +1,24 @@
 // mcg_server.cu -- continuous batching of solve requests (host runtime).
 //
 // A scheduler thread admits queued requests while their device buffers fit
-// the HBM budget, and advances every admitted request round by round on a
-// pool of CUDA streams: each round walks whole chunks of `chunk_paths` more
-// paths of each of the request's stations (path indices continue where the
-// last round stopped), reduces them into the request's station statistics,
-// finalizes and copies u, g_z, standard errors and path counts into pinned
-// host memory.  When a round's event has completed the thread decides on
-// the host whether the request reached its target; if not, it launches the
-// next round.  Rounds of different requests overlap on the GPU, so one
-// request's exit-time tail runs beside other requests' walks.
+// the HBM budget, and advances every admitted request round by round: each
+// round walks whole chunks of `chunk_paths` more paths of each of the
+// request's stations (path indices continue where the last round stopped),
+// reduces them into the request's station statistics, finalizes and copies
+// u, g_z, standard errors and path counts into pinned host memory.
+//
+// Rounds are launched in batches on a pool of stream slots, one batch in
+// flight per slot: the ready rounds of requests whose problems share every
+// scalar (domain, density and boundary kinds, grid geometry, step, h) go
+// into one walk launch -- a segment table gives each launch item its
+// request's stations, path range, generator key, status word and model
+// arrays -- followed by each request's own reduction.  The ready rounds are
+// spread over the free slots, so several launches are in flight and one
+// launch's exit-time tail runs beside the others.  When a batch has
+// completed the thread decides on the host, request by request, whether the
+// target is reached; if not, the request's next round joins a later batch.
+// A request's numbers depend only on its own seed, stations and target:
+// which batch a round runs in changes nothing.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -98,14 +107,16 @@ struct mcg_request {
     uint64_t seed = 0;
     // scheduler-thread state
     WalkParams P;
-    int stream = -1;
-    char* dev = nullptr;
+    std::vector<unsigned char> compat;  // requests with equal keys may share a walk launch
+    bool segable = false;               // its walk can run as a segment of a shared launch
+    char* dev = nullptr;                // stations | states | status word | results
     size_t bytes = 0;
+    int slot = -1;                      // slot of the last batch the request ran in
     int64_t round = 0;
     int64_t done_paths = 0;   // paths per station merged so far
-    int64_t round_paths = 0;  // paths per station of the round in flight
+    int64_t round_paths = 0;  // paths per station of the round planned / in flight
     bool in_flight = false;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;           // admission copies done
     double* h_res = nullptr;  // pinned: 6 S doubles + status word + 3 S station coordinates
     size_t h_cap = 0;         // capacity of the pinned block behind h_res
     std::shared_ptr<PinnedPool> pinned;
@@ -122,11 +133,22 @@ struct mcg_request {
     Clock::time_point t_submit, t_done;
 };
 
+// One stream with at most one batch of rounds in flight.
+struct ServerSlot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    mcg::WalkSeg* h_seg = nullptr;  // pinned: the batch's segment table, then its status word
+    std::vector<mcg_request*> reqs;
+    char* dev = nullptr;            // the batch's per-path buffers, walk scratch, table
+    size_t bytes = 0;
+    bool busy = false;
+};
+
 struct mcg_server {
     mcg_server_config cfg;
     int device = 0;
-    std::vector<cudaStream_t> streams;
-    std::vector<int> load;
+    std::vector<ServerSlot> slots;
+    cudaStream_t admit_st = nullptr;  // admission copies
     std::mutex mu;
     std::condition_variable cv;
     std::deque<mcg_request*> pending;
@@ -136,20 +158,23 @@ struct mcg_server {
     std::shared_ptr<PinnedPool> pinned = std::make_shared<PinnedPool>();
     cudaMemPool_t pool = nullptr;  // the server's own stream-ordered device pool
     std::thread th;
+    std::atomic<int64_t> n_launches{0}, n_rounds{0};  // walk launches, request rounds in them
 };
 
 namespace {
 
-// Device layout of a request: stations | states | status word + counter |
-// finalized results | per-path u, d, steps | walk scratch.
-struct Layout {
-    size_t st, states, status, res, u, d, steps, work, total;
+constexpr int kMaxSeg = 64;                         // requests in one walk launch at most
+constexpr unsigned long long kMinBatchItems = 1ull << 18;  // smaller batches do not fill the GPU
+
+// Device layout of a request: stations | states | status word | results.
+struct ReqLayout {
+    size_t st, states, status, res, total;
 };
 
-Layout layout(int64_t S, int64_t chunk, int precision)
+ReqLayout req_layout(int64_t S)
 {
-    Layout L;
-    const size_t s = (size_t)S, n = (size_t)S * (size_t)chunk;
+    ReqLayout L;
+    const size_t s = (size_t)S;
     size_t o = 0;
     L.st = o;
     o += align256(s * 3 * sizeof(double));
@@ -159,16 +184,49 @@ Layout layout(int64_t S, int64_t chunk, int precision)
     o += 256;
     L.res = o;
     o += align256(s * 6 * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+// Device layout of a batch of n items: per-path u, d, steps | work counter +
+// batch status word | segment table | walk scratch.
+struct BatchLayout {
+    size_t u, d, steps, ctr, seg, work, total;
+};
+
+BatchLayout batch_layout(size_t n, int precision)
+{
+    BatchLayout L;
+    size_t o = 0;
     L.u = o;
     o += align256(n * sizeof(double));
     L.d = o;
     o += align256(n * sizeof(double));
     L.steps = o;
     o += align256(n * sizeof(int64_t));
+    L.ctr = o;
+    o += 256;
+    L.seg = o;
+    o += align256(kMaxSeg * sizeof(WalkSeg));
     L.work = o;
-    o += mcg_walk_work_bytes(S, chunk, precision);
+    o += mcg_walk_work_bytes(1, (int64_t)n, precision);
     L.total = o;
     return L;
+}
+
+// The problem scalars of a request with its own data (stations, key, model
+// arrays, status) masked out: requests with equal keys can share a walk
+// launch (the launch takes its scalars from any of them).
+std::vector<unsigned char> compat_key(const WalkParams& P0)
+{
+    WalkParams P = P0;  // make_params zeroed every byte first, padding included
+    P.key0 = P.key1 = 0;
+    P.grid = nullptr;
+    P.zq = P.zq ? (const float4*)16 : nullptr;  // packed or not selects the kernel
+    P.faces = nullptr;
+    P.tq = P.tq ? (const float4*)16 : nullptr;
+    const unsigned char* b = (const unsigned char*)&P;
+    return std::vector<unsigned char>(b, b + sizeof(P));
 }
 
 void finish(mcg_request* r, int status, const char* msg)
@@ -213,49 +271,112 @@ int64_t next_round_paths(const mcg_server* sv, const mcg_request* r)
     return n > 0 ? n : chunk;
 }
 
-// Launches the request's next round on its stream.
-int launch_round(mcg_server* sv, mcg_request* r)
+// Launches one batch of rounds (each request's round_paths already planned)
+// on slot `k`: one walk over all their items, then per request its reduction,
+// finalize and result copies, then the slot's event.  A batch of one request
+// is a plain launch of that request's problem.  Returns MCG_ERR_OOM when the
+// batch's buffers do not fit now (nothing launched).
+int launch_batch(mcg_server* sv, int k, const std::vector<mcg_request*>& reqs)
 {
-    const int64_t chunk = next_round_paths(sv, r);
-    const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
-    cudaStream_t st = sv->streams[r->stream];
-    WalkParams P = r->P;
-    P.stations = (const double*)(r->dev + L.st);
-    P.S = r->S;
-    P.N = chunk;
-    P.p0 = r->done_paths;
-    P.total = (unsigned long long)r->S * (unsigned long long)chunk;
-    P.pp_u = (double*)(r->dev + L.u);
-    P.pp_d = (double*)(r->dev + L.d);
-    P.pp_steps = (int64_t*)(r->dev + L.steps);
-    P.status = (int32_t*)(r->dev + L.status);
-    P.counter = (unsigned long long*)(r->dev + L.status + 128);
-    if (sv->cfg.walk.precision == MCG_MIXED) bind_work(P, r->dev + L.work, sv->cfg.walk.migrate != 0);
-    r->round_paths = chunk;
-    mcg_station_state* states = (mcg_station_state*)(r->dev + L.states);
-    double* res = (double*)(r->dev + L.res);
-    cudaError_t e;
-    if ((e = reset_walk(P, st)) ||
-        (e = launch_walk(P, sv->cfg.walk.precision, sv->cfg.walk.block ? sv->cfg.walk.block : 128, st)) ||
-        (e = launch_reduce(P.pp_u, P.pp_d, P.pp_steps, r->S, chunk, states, st)) ||
-        (e = launch_finalize(states, r->S, res, res + r->S, res + 2 * r->S, res + 3 * r->S, (int64_t*)(res + 4 * r->S),
-                             (int64_t*)(res + 5 * r->S), st)) ||
-        (e = cudaMemcpyAsync(r->h_res, res, 6 * r->S * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(r->h_res + 6 * r->S, P.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaEventRecord(r->ev, st)))
-        return set_error(MCG_ERR_CUDA, "round launch: %s", cudaGetErrorString(e));
-    r->in_flight = true;
+    ServerSlot& sl = sv->slots[k];
+    cudaStream_t st = sl.st;
+    const int prec = sv->cfg.walk.precision;
+    std::vector<unsigned long long> begin(reqs.size());
+    unsigned long long T = 0;
+    for (size_t i = 0; i < reqs.size(); ++i) {
+        begin[i] = T;
+        T += (unsigned long long)reqs[i]->S * (unsigned long long)reqs[i]->round_paths;
+    }
+    const BatchLayout L = batch_layout((size_t)T, prec);
+    cudaError_t e = cudaMallocFromPoolAsync((void**)&sl.dev, L.total, sv->pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sl.dev = nullptr;
+        return MCG_ERR_OOM;
+    }
+    sl.bytes = L.total;
+    WalkParams P = reqs[0]->P;
+    P.total = T;
+    P.pp_u = (double*)(sl.dev + L.u);
+    P.pp_d = (double*)(sl.dev + L.d);
+    P.pp_steps = (int64_t*)(sl.dev + L.steps);
+    P.counter = (unsigned long long*)(sl.dev + L.ctr);
+    int32_t* bstatus = (int32_t*)(sl.dev + L.ctr + 128);
+    if (prec == MCG_MIXED) bind_work(P, sl.dev + L.work, sv->cfg.walk.migrate != 0);
+    int32_t* h_bstatus = (int32_t*)(sl.h_seg + kMaxSeg);
+    *h_bstatus = 0;
+    const ReqLayout R0 = req_layout(reqs[0]->S);
+    if (reqs.size() == 1) {  // the request's own problem, as a plain launch
+        mcg_request* r = reqs[0];
+        P.stations = (const double*)(r->dev + R0.st);
+        P.S = r->S;
+        P.N = r->round_paths;
+        P.p0 = r->done_paths;
+        P.status = (int32_t*)(r->dev + R0.status);
+    } else {
+        for (size_t i = 0; i < reqs.size(); ++i) {
+            const mcg_request* r = reqs[i];
+            const ReqLayout RL = req_layout(r->S);
+            WalkSeg& g = sl.h_seg[i];
+            g.begin = begin[i];
+            g.stations = (const double*)(r->dev + RL.st);
+            g.N = r->round_paths;
+            g.p0 = r->done_paths;
+            g.status = (int32_t*)(r->dev + RL.status);
+            g.grid = r->P.grid;
+            g.zq = r->P.zq;
+            g.faces = r->P.faces;
+            g.tq = r->P.tq;
+            g.key0 = r->P.key0;
+            g.key1 = r->P.key1;
+        }
+        P.stations = nullptr;
+        P.S = 0;
+        P.N = 1;
+        P.p0 = 0;
+        P.status = bstatus;  // what no single request can be blamed for (a lost walk)
+        P.seg = (const WalkSeg*)(sl.dev + L.seg);
+        P.nseg = (int32_t)reqs.size();
+        if ((e = cudaMemcpyAsync(sl.dev + L.seg, sl.h_seg, reqs.size() * sizeof(WalkSeg), cudaMemcpyHostToDevice, st)))
+            return set_error(MCG_ERR_CUDA, "segment table: %s", cudaGetErrorString(e));
+    }
+    for (mcg_request* r : reqs)  // the first round waits for the admission copies
+        if (r->round == 0 && (e = cudaStreamWaitEvent(st, r->ev, 0)))
+            return set_error(MCG_ERR_CUDA, "admission order: %s", cudaGetErrorString(e));
+    if ((e = cudaMemsetAsync(bstatus, 0, sizeof(int32_t), st)) || (e = reset_walk(P, st)) ||
+        (e = launch_walk(P, prec, sv->cfg.walk.block ? sv->cfg.walk.block : 128, st)))
+        return set_error(MCG_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < reqs.size(); ++i) {
+        mcg_request* r = reqs[i];
+        const ReqLayout RL = req_layout(r->S);
+        mcg_station_state* states = (mcg_station_state*)(r->dev + RL.states);
+        double* res = (double*)(r->dev + RL.res);
+        if ((e = launch_reduce(P.pp_u + begin[i], P.pp_d + begin[i], P.pp_steps + begin[i], r->S, r->round_paths,
+                               states, st)) ||
+            (e = launch_finalize(states, r->S, res, res + r->S, res + 2 * r->S, res + 3 * r->S,
+                                 (int64_t*)(res + 4 * r->S), (int64_t*)(res + 5 * r->S), st)) ||
+            (e = cudaMemcpyAsync(r->h_res, res, 6 * r->S * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(r->h_res + 6 * r->S, r->dev + RL.status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 st)))
+            return set_error(MCG_ERR_CUDA, "round reduction: %s", cudaGetErrorString(e));
+        r->in_flight = true;
+        r->slot = k;
+    }
+    if ((e = cudaMemcpyAsync(h_bstatus, bstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaEventRecord(sl.ev, st)))
+        return set_error(MCG_ERR_CUDA, "batch event: %s", cudaGetErrorString(e));
+    sl.reqs = reqs;
+    sl.busy = true;
+    sv->used += sl.bytes;
+    sv->n_launches.fetch_add(1);
+    sv->n_rounds.fetch_add((int64_t)reqs.size());
     return MCG_OK;
 }
 
 int admit(mcg_server* sv, mcg_request* r)
 {
-    int best = 0;
-    for (int i = 1; i < (int)sv->streams.size(); ++i)
-        if (sv->load[i] < sv->load[best]) best = i;
-    r->stream = best;
-    cudaStream_t st = sv->streams[best];
-    const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
+    cudaStream_t st = sv->admit_st;
+    const ReqLayout L = req_layout(r->S);
     cudaError_t e = cudaMallocFromPoolAsync((void**)&r->dev, L.total, sv->pool, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -268,12 +389,11 @@ int admit(mcg_server* sv, mcg_request* r)
     if ((e = cudaMemcpyAsync(r->dev + L.st, r->h_res + 6 * r->S + 1, r->S * 3 * sizeof(double),
                              cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemsetAsync(r->dev + L.states, 0, r->S * sizeof(mcg_station_state), st)) ||
-        (e = cudaMemsetAsync(r->dev + L.status, 0, 256, st))) {
+        (e = cudaMemsetAsync(r->dev + L.status, 0, 256, st)) || (e = cudaEventRecord(r->ev, st))) {
         cudaFreeAsync(r->dev, st);
         r->dev = nullptr;
         return MCG_ERR_CUDA;
     }
-    sv->load[best]++;
     sv->used += L.total;
     return MCG_OK;
 }
@@ -281,10 +401,10 @@ int admit(mcg_server* sv, mcg_request* r)
 void release(mcg_server* sv, mcg_request* r)
 {
     if (r->dev) {
-        cudaFreeAsync(r->dev, sv->streams[r->stream]);
+        // after the last batch that used it (or the admission copies)
+        cudaFreeAsync(r->dev, r->slot >= 0 ? sv->slots[r->slot].st : sv->admit_st);
         r->dev = nullptr;
         sv->used -= r->bytes;
-        sv->load[r->stream]--;
     }
 }
 
@@ -300,6 +420,124 @@ bool reached(const mcg_server* sv, const mcg_request* r, int64_t n)
     return true;
 }
 
+void retire(mcg_server* sv, mcg_request* r)
+{
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (size_t i = 0; i < sv->active.size(); ++i)
+        if (sv->active[i] == r) {
+            sv->active.erase(sv->active.begin() + i);
+            break;
+        }
+}
+
+// A batch has completed (q: its event's status): every request in it either
+// ends (target, cap, cancel, error) or becomes ready for its next round.
+// After finish() the caller may free a request at any moment: nothing here
+// touches it again once it has been finished.
+void complete_batch(mcg_server* sv, ServerSlot& sl, cudaError_t q)
+{
+    const int32_t bbits = *(const int32_t*)(sl.h_seg + kMaxSeg);
+    for (mcg_request* r : sl.reqs) {
+        r->in_flight = false;
+        int end = -1;  // status that ends the request, -1: continue
+        const char* msg = nullptr;
+        if (q != cudaSuccess) {
+            end = MCG_ERR_CUDA;
+            msg = cudaGetErrorString(q);
+        } else {
+            r->round++;
+            r->rounds.store(r->round);
+            r->done_paths += r->round_paths;
+            int64_t n = 0;
+            std::memcpy(&n, r->h_res + 4 * r->S, sizeof(int64_t));
+            r->paths.store(n);
+            int32_t bits = 0;
+            std::memcpy(&bits, r->h_res + 6 * r->S, sizeof(int32_t));
+            bits |= bbits;
+            if (bits) {
+                end = status_from_bits(bits);  // never MCG_OK for a nonzero word
+                msg = "walk status";
+            } else if (r->cancel.load()) {
+                end = MCG_ERR_CANCELLED;
+                msg = "cancelled";
+            } else if (reached(sv, r, n)) {
+                end = MCG_OK;
+            }
+        }
+        if (end >= 0) {
+            release(sv, r);
+            retire(sv, r);
+            finish(r, end, msg);
+        }
+    }
+    cudaFreeAsync(sl.dev, sl.st);
+    sl.dev = nullptr;
+    sv->used -= sl.bytes;
+    sl.bytes = 0;
+    sl.reqs.clear();
+    sl.busy = false;
+}
+
+// Forms batches of the ready rounds for the free slots: the planned items of
+// all ready rounds are spread evenly over the free slots (at least
+// kMinBatchItems, at most cfg.batch_items per batch, one request at least),
+// each batch holding requests of one compatibility key in admission order.
+bool form_batches(mcg_server* sv, std::vector<mcg_request*>& ready)
+{
+    std::vector<int> free_slots;
+    for (int k = 0; k < (int)sv->slots.size(); ++k)
+        if (!sv->slots[k].busy) free_slots.push_back(k);
+    if (ready.empty() || free_slots.empty()) return false;
+    unsigned long long total = 0;
+    for (mcg_request* r : ready) {
+        r->round_paths = next_round_paths(sv, r);
+        total += (unsigned long long)r->S * (unsigned long long)r->round_paths;
+    }
+    unsigned long long per = (total + free_slots.size() - 1) / free_slots.size();
+    const unsigned long long cap = sv->cfg.batch ? (unsigned long long)sv->cfg.batch_items : 0ull;
+    if (per < kMinBatchItems) per = kMinBatchItems;
+    if (per > cap) per = cap;
+    bool progressed = false;
+    size_t f = 0;
+    while (!ready.empty() && f < free_slots.size()) {
+        mcg_request* r0 = ready.front();
+        std::vector<mcg_request*> batch{r0};
+        unsigned long long items = (unsigned long long)r0->S * (unsigned long long)r0->round_paths;
+        std::vector<mcg_request*> rest;
+        for (size_t i = 1; i < ready.size(); ++i) {
+            mcg_request* r = ready[i];
+            const unsigned long long n = (unsigned long long)r->S * (unsigned long long)r->round_paths;
+            if (sv->cfg.batch && r0->segable && r->segable && batch.size() < (size_t)kMaxSeg && items < per &&
+                items + n <= cap && r->compat == r0->compat) {
+                batch.push_back(r);
+                items += n;
+            } else {
+                rest.push_back(r);
+            }
+        }
+        // the batch's buffers must fit the budget unless nothing else is in flight
+        bool any_busy = false;
+        for (const ServerSlot& sl : sv->slots) any_busy = any_busy || sl.busy;
+        if (any_busy && sv->used + batch_layout((size_t)items, sv->cfg.walk.precision).total >
+                            (size_t)sv->cfg.hbm_budget)
+            break;
+        const int rc = launch_batch(sv, free_slots[f], batch);
+        if (rc == MCG_ERR_OOM && any_busy) break;  // retry when a batch frees its buffers
+        if (rc != MCG_OK) {
+            for (mcg_request* r : batch) {
+                release(sv, r);
+                retire(sv, r);
+                finish(r, rc == MCG_ERR_OOM ? MCG_ERR_OOM : MCG_ERR_CUDA, "round launch failed");
+            }
+        } else {
+            ++f;
+        }
+        progressed = true;
+        ready.swap(rest);
+    }
+    return progressed;
+}
+
 void scheduler(mcg_server* sv)
 {
     cudaSetDevice(sv->device);
@@ -311,8 +549,8 @@ void scheduler(mcg_server* sv)
             // admission: FIFO, while the budget and the slot count allow
             while (!sv->pending.empty() && (int)sv->active.size() < sv->cfg.max_active) {
                 mcg_request* r = sv->pending.front();
-                const Layout L = layout(r->S, sv->cfg.max_round_paths, sv->cfg.walk.precision);
-                if (!sv->active.empty() && sv->used + L.total > (size_t)sv->cfg.hbm_budget) break;
+                const size_t need = req_layout(r->S).total;
+                if (!sv->active.empty() && sv->used + need > (size_t)sv->cfg.hbm_budget) break;
                 sv->pending.pop_front();
                 lk.unlock();
                 const int rc = admit(sv, r);
@@ -328,73 +566,33 @@ void scheduler(mcg_server* sv)
                 progressed = true;
             }
         }
-        // advance the admitted requests
-        std::vector<mcg_request*> act;
+        // completed batches
+        for (ServerSlot& sl : sv->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev);
+            if (q == cudaErrorNotReady) continue;
+            complete_batch(sv, sl, q);
+            progressed = true;
+        }
+        // the ready rounds: admitted requests not in flight; a cancelled one
+        // ends here once it has results of at least one round
+        std::vector<mcg_request*> act, ready;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             act = sv->active;
         }
-        // After finish() the caller may free the request at any moment: the
-        // loop below never touches `r` again once it has been finished.
-        auto retire = [sv](mcg_request* r) {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            for (size_t i = 0; i < sv->active.size(); ++i)
-                if (sv->active[i] == r) {
-                    sv->active.erase(sv->active.begin() + i);
-                    break;
-                }
-        };
         for (mcg_request* r : act) {
-            if (r->in_flight) {
-                const cudaError_t q = cudaEventQuery(r->ev);
-                if (q == cudaErrorNotReady) continue;
-                r->in_flight = false;
-                progressed = true;
-                int end = -1;  // status that ends the request, -1: continue
-                const char* msg = nullptr;
-                if (q != cudaSuccess) {
-                    end = MCG_ERR_CUDA;
-                    msg = cudaGetErrorString(q);
-                } else {
-                    r->round++;
-                    r->rounds.store(r->round);
-                    r->done_paths += r->round_paths;
-                    int64_t n = 0;
-                    std::memcpy(&n, r->h_res + 4 * r->S, sizeof(int64_t));
-                    r->paths.store(n);
-                    int32_t bits = 0;
-                    std::memcpy(&bits, r->h_res + 6 * r->S, sizeof(int32_t));
-                    if (bits) {
-                        end = status_from_bits(bits);
-                        msg = "walk status";
-                    } else if (r->cancel.load()) {
-                        end = MCG_ERR_CANCELLED;
-                        msg = "cancelled";
-                    } else if (reached(sv, r, n)) {
-                        end = MCG_OK;
-                    }
-                }
-                if (end >= 0) {
-                    release(sv, r);
-                    retire(r);
-                    finish(r, end, msg);
-                    continue;
-                }
-            }
+            if (r->in_flight) continue;
             if (r->cancel.load() && r->round > 0) {
                 release(sv, r);
-                retire(r);
+                retire(sv, r);
                 finish(r, MCG_ERR_CANCELLED, "cancelled");
+                progressed = true;
                 continue;
             }
-            if (launch_round(sv, r) != MCG_OK) {
-                release(sv, r);
-                retire(r);
-                finish(r, MCG_ERR_CUDA, "round launch failed");
-                continue;
-            }
-            progressed = true;
+            ready.push_back(r);
         }
+        if (form_batches(sv, ready)) progressed = true;
         if (!progressed) {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv.wait_for(lk, std::chrono::microseconds(50));
@@ -418,6 +616,8 @@ void mcg_server_config_default(mcg_server_config* c)
     c->max_paths = 10000000;
     c->max_round_paths = 16 * 4096;
     mcg_options_default(&c->walk);
+    c->batch = 1;
+    c->batch_items = (int64_t)1 << 22;
 }
 
 int mcg_model_create(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary, double dt,
@@ -522,6 +722,8 @@ int mcg_server_create(const mcg_server_config* cfg_in, mcg_server** out)
     cfg.max_round_paths -= cfg.max_round_paths % cfg.chunk_paths;
     if (cfg.walk.precision != MCG_FP64 && cfg.walk.precision != MCG_MIXED)
         return set_error(MCG_ERR_ARG, "walk.precision must be MCG_FP64 or MCG_MIXED");
+    if (cfg.batch != 0 && cfg.batch != 1) return set_error(MCG_ERR_ARG, "batch must be 0 or 1");
+    if (cfg.batch && cfg.batch_items <= 0) return set_error(MCG_ERR_ARG, "batch_items must be positive");
     mcg_server* sv = new mcg_server();
     sv->cfg = cfg;
     cudaGetDevice(&sv->device);
@@ -549,17 +751,28 @@ int mcg_server_create(const mcg_server_config* cfg_in, mcg_server** out)
         int off = 0;
         cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowInternalDependencies, &off);
     }
-    for (int i = 0; i < cfg.streams; ++i) {
-        cudaStream_t st;
-        const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            for (cudaStream_t s2 : sv->streams) cudaStreamDestroy(s2);
-            cudaMemPoolDestroy(sv->pool);
-            delete sv;
-            return set_error(MCG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    // the stream slots (each with its pinned segment table and status word)
+    // and the admission stream
+    cudaError_t e = cudaStreamCreateWithFlags(&sv->admit_st, cudaStreamNonBlocking);
+    sv->slots.resize(cfg.streams);
+    for (int i = 0; i < cfg.streams && e == cudaSuccess; ++i) {
+        ServerSlot& sl = sv->slots[i];
+        if ((e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) ||
+            (e = cudaMallocHost((void**)&sl.h_seg, kMaxSeg * sizeof(WalkSeg) + 256)))
+            break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (ServerSlot& sl : sv->slots) {
+            if (sl.st) cudaStreamDestroy(sl.st);
+            if (sl.ev) cudaEventDestroy(sl.ev);
+            if (sl.h_seg) cudaFreeHost(sl.h_seg);
         }
-        sv->streams.push_back(st);
-        sv->load.push_back(0);
+        if (sv->admit_st) cudaStreamDestroy(sv->admit_st);
+        cudaMemPoolDestroy(sv->pool);
+        delete sv;
+        return set_error(MCG_ERR_CUDA, "server streams: %s", cudaGetErrorString(e));
     }
     sv->th = std::thread(scheduler, sv);
     *out = sv;
@@ -575,10 +788,14 @@ int mcg_server_destroy(mcg_server* sv)
     }
     sv->cv.notify_all();
     sv->th.join();
-    for (cudaStream_t st : sv->streams) {
-        cudaStreamSynchronize(st);
-        cudaStreamDestroy(st);
+    for (ServerSlot& sl : sv->slots) {
+        cudaStreamSynchronize(sl.st);
+        cudaStreamDestroy(sl.st);
+        cudaEventDestroy(sl.ev);
+        cudaFreeHost(sl.h_seg);
     }
+    cudaStreamSynchronize(sv->admit_st);
+    cudaStreamDestroy(sv->admit_st);
     cudaMemPoolDestroy(sv->pool);
     delete sv;
     return MCG_OK;
@@ -601,6 +818,8 @@ int mcg_submit(mcg_server* sv, const mcg_model* m, const double* stations, int64
         delete r;
         return rc;
     }
+    r->compat = compat_key(r->P);
+    r->segable = !r->P.ball && !r->P.bridge;
     r->server = sv;
     r->model = m;
     r->S = S;
@@ -692,6 +911,14 @@ int mcg_request_info(const mcg_request* r, int64_t* paths, int64_t* rounds, doub
         const Clock::time_point t = r->done ? r->t_done : Clock::now();
         *seconds = std::chrono::duration<double>(t - r->t_submit).count();
     }
+    return MCG_OK;
+}
+
+int mcg_server_stats(const mcg_server* s, int64_t* launches, int64_t* rounds)
+{
+    if (!s) return set_error(MCG_ERR_ARG, "null server");
+    if (launches) *launches = s->n_launches.load();
+    if (rounds) *rounds = s->n_rounds.load();
     return MCG_OK;
 }
 

@@ -65,9 +65,10 @@ __device__ __forceinline__ bool refill(const WalkParams& P, bool busy, bool& exh
 
 // A station whose walk copies are not all strictly inside Omega gets NaN
 // and the MCG_ERR_ARG bit (mcgrav_solve rejects such stations up front).
-__device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsigned long long item)
+__device__ __forceinline__ bool station_ok(const WalkParams& P, const double* stations, int32_t* status, uint32_t s,
+                                           unsigned long long item)
 {
-    const double x = P.stations[3 * s], y = P.stations[3 * s + 1], z = P.stations[3 * s + 2];
+    const double x = stations[3 * s], y = stations[3 * s + 1], z = stations[3 * s + 2];
     bool ok;
     if (P.ball) {
         const double dx = x - P.cen[0], dy = y - P.cen[1], dz = z - P.cen[2];
@@ -82,7 +83,7 @@ __device__ __forceinline__ bool station_ok(const WalkParams& P, uint32_t s, unsi
         P.pp_d[item] = kNaN;
         P.pp_steps[item] = 0;
         if (P.drec) P.drec[item] = no_record();  // the exit kernel then writes NaN too
-        atomicOr(P.status, 1 << MCG_ERR_ARG);
+        atomicOr(status, 1 << MCG_ERR_ARG);
     }
     return ok;
 }
@@ -216,7 +217,7 @@ __device__ __forceinline__ double ball_theta(const double* q, const double* dW, 
 // its first boundary crossing (lowest axis on ties), closes the trapezoid
 // over the clipped part and returns g(x*) - 2 pi G I.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ double exit_fp64(const WalkParams& P, const double* X, const double* dW,
+__device__ __noinline__ double exit_fp64(const WalkParams& P, const ModelRef& M, const double* X, const double* dW,
                                          const double* Y, double I, double rp)
 {
     double xs[3];
@@ -251,9 +252,9 @@ __device__ __noinline__ double exit_fp64(const WalkParams& P, const double* X, c
         xs[1] = Y[1];
         xs[2] = Y[2];
     }
-    const double r = rho_f64(P, xs);
+    const double r = rho_f64(P, M, xs);
     I = __dadd_rn(I, __dmul_rn(__dmul_rn(__dmul_rn(0.5, __dadd_rn(rp, r)), theta), P.dt));
-    return __dadd_rn(boundary_value(P, face, xs), -__dmul_rn(P.two_pi_G, I));
+    return __dadd_rn(boundary_value(P, M, face, xs), -__dmul_rn(P.two_pi_G, I));
 }
 
 // Mixed walk exit (run by exit_mixed_kernel, one thread per path, so the
@@ -261,8 +262,8 @@ __device__ __noinline__ double exit_fp64(const WalkParams& P, const double* X, c
 // single precision as the walk computed them; the flushed + partial sums give
 // S = rho_0 / 2 + sum_{n=1}^{N-1} rho_n, so the trapezoid integral over the
 // inside steps is dt (S - rho_{N-1} / 2).
-__device__ __forceinline__ double exit_mixed(const WalkParams& P, const float* Xf, const float* Yf, double flushed,
-                                             float partial, float rp)
+__device__ __forceinline__ double exit_mixed(const WalkParams& P, const ModelRef& M, const float* Xf, const float* Yf,
+                                             double flushed, float partial, float rp)
 {
     const double acc = flushed + (double)partial;
     double X[3], dW[3], xs[3];
@@ -296,10 +297,10 @@ __device__ __forceinline__ double exit_mixed(const WalkParams& P, const float* X
     } else {
         for (int k = 0; k < 3; ++k) xs[k] = P.cen[k] + (double)Yf[k];
     }
-    const double r = rho_f64(P, xs);
+    const double r = rho_f64(P, M, xs);
     const double rpd = (double)rp;
     const double I = P.dt * (acc - 0.5 * rpd) + 0.5 * theta * P.dt * (rpd + r);
-    return boundary_value(P, face, xs) - P.two_pi_G * I;
+    return boundary_value(P, M, face, xs) - P.two_pi_G * I;
 }
 
 // Exit records of the mixed walk (structure of arrays, item-major):
@@ -323,15 +324,15 @@ __device__ __forceinline__ void put_exit(const WalkParams& P, int c, unsigned lo
     P.drec[(size_t)c * T + item] = flushed;
 }
 
-__device__ __forceinline__ void write_path(const WalkParams& P, unsigned long long item, double u0, double up,
-                                           double um, int64_t steps)
+__device__ __forceinline__ void write_path(const WalkParams& P, int32_t* status, unsigned long long item, double u0,
+                                           double up, double um, int64_t steps)
 {
     const double d = P.crn ? (up - um) / (2.0 * P.h) : kNaN;
     P.pp_u[item] = u0;
     P.pp_d[item] = d;
     P.pp_steps[item] = steps;
     const bool bad = !isfinite(u0) || (P.crn && !isfinite(d));
-    if (bad) atomicOr(P.status, 1 << MCG_ERR_NONFINITE);
+    if (bad) atomicOr(status, 1 << MCG_ERR_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,7 +414,7 @@ __device__ __noinline__ unsigned bridge_exits_f32(const WalkParams& P, unsigned 
 // ---------------------------------------------------------------------------
 // Plain double-precision walk.
 // ---------------------------------------------------------------------------
-template <bool CRN>
+template <bool CRN, bool SEG>
 __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 {
     constexpr int NC = CRN ? 3 : 1;
@@ -426,6 +427,10 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
     int64_t steps = 0;
     const double off[3] = {0.0, P.h, -P.h};
     unsigned iter = 0u;
+    // the walk's request (its own in a multi-request launch)
+    uint32_t k0 = P.key0, k1 = P.key1;
+    int32_t* status = P.status;
+    ModelRef M = model_of(P);
 
     for (;;) {
         if ((++iter & 255u) == 0u && cancelled(P)) {
@@ -438,26 +443,41 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
             busy = false;
             exhausted = true;
         }
-        if (refill(P, busy, exhausted, item) &&
-            station_ok(P, s = (uint32_t)(item / (unsigned long long)P.N), item)) {
-            p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
-            for (int k = 0; k < 3; ++k) W[k] = P.stations[3 * s + k];
-            for (int c = 0; c < NC; ++c) {
-                const double X[3] = {W[0], W[1], __dadd_rn(W[2], off[c])};
-                rp[c] = rho_f64(P, X);
-                I[c] = 0.0;
+        if (refill(P, busy, exhausted, item)) {
+            const double* st = P.stations;
+            unsigned long long local = item, N = (unsigned long long)P.N, p0 = (unsigned long long)P.p0;
+            if constexpr (SEG) {
+                const WalkSeg& g = P.seg[find_seg(P, item)];
+                local = item - g.begin;
+                N = (unsigned long long)g.N;
+                p0 = (unsigned long long)g.p0;
+                st = g.stations;
+                status = g.status;
+                k0 = g.key0;
+                k1 = g.key1;
+                M = model_of(g);
             }
-            u[0] = u[1] = u[2] = kNaN;
-            alive = (1u << NC) - 1u;
-            n = 0;
-            steps = 0;
-            busy = true;
+            s = (uint32_t)(local / N);
+            if (station_ok(P, st, status, s, item)) {
+                p = (uint32_t)(p0 + local % N);
+                for (int k = 0; k < 3; ++k) W[k] = st[3 * s + k];
+                for (int c = 0; c < NC; ++c) {
+                    const double X[3] = {W[0], W[1], __dadd_rn(W[2], off[c])};
+                    rp[c] = rho_f64(P, M, X);
+                    I[c] = 0.0;
+                }
+                u[0] = u[1] = u[2] = kNaN;
+                alive = (1u << NC) - 1u;
+                n = 0;
+                steps = 0;
+                busy = true;
+            }
         }
         if (!__any_sync(kFull, busy)) break;
         if (!busy) continue;
 
         double z[12];
-        normals12_f64(s, p, (uint32_t)(n >> 2), P.key0, P.key1, z);
+        normals12_f64(s, p, (uint32_t)(n >> 2), k0, k1, z);
 #pragma unroll 1
         for (int m = 0; m < 4 && alive; ++m) {
             const double dW[3] = {__dmul_rn(P.sd, z[3 * m]), __dmul_rn(P.sd, z[3 * m + 1]),
@@ -478,21 +498,22 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
                     inside = Y[0] > P.lo[0] && Y[0] < P.hi[0] && Y[1] > P.lo[1] && Y[1] < P.hi[1] && Y[2] > P.lo[2] &&
                              Y[2] < P.hi[2];
                 }
-                const int kb = (inside && P.bridge) ? bridge_face_f64(P, X, Y, s, p, (uint32_t)n) : -1;
+                // (multi-request launches run without the bridge test)
+                const int kb = (!SEG && inside && P.bridge) ? bridge_face_f64(P, X, Y, s, p, (uint32_t)n) : -1;
                 if (inside && kb < 0) {
-                    const double r = rho_f64(P, Y);
+                    const double r = rho_f64(P, M, Y);
                     I[c] = __dadd_rn(I[c], __dmul_rn(__dmul_rn(0.5, __dadd_rn(rp[c], r)), P.dt));
                     rp[c] = r;
                 } else if (inside) {
                     // the bridge left Omega: end on face kb below Y after a full step
                     double xs[3] = {Y[0], Y[1], Y[2]};
                     xs[kb >> 1] = (kb & 1) ? P.hi[kb >> 1] : P.lo[kb >> 1];
-                    const double r = rho_f64(P, xs);
+                    const double r = rho_f64(P, M, xs);
                     const double Ic = __dadd_rn(I[c], __dmul_rn(__dmul_rn(0.5, __dadd_rn(rp[c], r)), P.dt));
-                    u[c] = __dadd_rn(boundary_value(P, kb, xs), -__dmul_rn(P.two_pi_G, Ic));
+                    u[c] = __dadd_rn(boundary_value(P, M, kb, xs), -__dmul_rn(P.two_pi_G, Ic));
                     alive &= ~(1u << c);
                 } else {
-                    u[c] = exit_fp64(P, X, dW, Y, I[c], rp[c]);
+                    u[c] = exit_fp64(P, M, X, dW, Y, I[c], rp[c]);
                     alive &= ~(1u << c);
                 }
             }
@@ -502,10 +523,10 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
             ++n;
         }
         if (!alive) {
-            write_path(P, item, u[0], u[1], u[2], steps);
+            write_path(P, status, item, u[0], u[1], u[2], steps);
             busy = false;
         } else if (n >= P.max_steps) {
-            atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
+            atomicOr(status, 1 << MCG_ERR_STEP_CAP);
             P.pp_u[item] = kNaN;
             P.pp_d[item] = kNaN;
             P.pp_steps[item] = steps;
@@ -524,15 +545,21 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 // sums (a real, warp-uniform branch, so the slow double-precision unit sees
 // one instruction per copy per 64 steps).
 // ---------------------------------------------------------------------------
-template <int RHO, bool CRN, bool BRIDGE, bool BALL>
+//
+// SEG: a multi-request launch (the segment table maps each item to its
+// request); each lane then carries its walk's generator key and model array,
+// and keeps the segment index with the walk's other cold state.
+template <int RHO, bool CRN, bool BRIDGE, bool BALL, bool SEG>
 __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const WalkParams P)
 {
+    static_assert(!(SEG && (BRIDGE || BALL)), "multi-request launches use the box without the bridge test");
     // Per-walk state touched only at refills, exits and flushes lives in
     // shared memory (one slot per thread); the step loop keeps the position,
     // the partial sums, the path indices and the live-copy mask in registers.
     __shared__ double sh_D[3][128];              // flushed sums per copy
     __shared__ unsigned long long sh_item[128];  // work item of the walk
     __shared__ long long sh_steps[128];          // EM steps of the copies that have exited
+    __shared__ int sh_seg[SEG ? 128 : 1];        // segment of the walk (multi-request launch)
     const int t = threadIdx.x;
     bool busy = false, exhausted = false;
     uint32_t s = 0u, p = 0u, blk = 0u;
@@ -547,6 +574,19 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
     const bool migrate = P.pool != nullptr;
     bool stop = false;     // cancelled: take no more work of any kind
     bool spilled = false;  // this warp has spilled its walks once
+    uint32_t k0 = P.key0, k1 = P.key1;  // generator key of the lane's walk
+    ModelRef M = model_of(P);           // model arrays of the lane's walk
+    // the lane's walk now belongs to the request of launch item `it`
+    auto adopt = [&](unsigned long long it) {
+        if constexpr (SEG) {
+            const int gi = find_seg(P, it);
+            const WalkSeg& g = P.seg[gi];
+            k0 = g.key0;
+            k1 = g.key1;
+            M = model_of(g);
+            sh_seg[t] = gi;
+        }
+    };
 
     for (;;) {
         if ((++round & 15u) == 0u && cancelled(P)) {
@@ -562,14 +602,30 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             stop = true;
         }
         unsigned long long item = 0ull;
-        if (refill(P, busy, exhausted, item) &&
-            station_ok(P, s = (uint32_t)(item / (unsigned long long)P.N), item)) {
-            p = (uint32_t)((unsigned long long)P.p0 + item % (unsigned long long)P.N);
-            wx = (float)(P.stations[3 * s + 0] - P.cen[0]);
-            wy = (float)(P.stations[3 * s + 1] - P.cen[1]);
-            wz = (float)(P.stations[3 * s + 2] - P.cen[2]);
+        bool start = refill(P, busy, exhausted, item);
+        const double* st = P.stations;
+        if (start) {
+            unsigned long long local = item, N = (unsigned long long)P.N, p0 = (unsigned long long)P.p0;
+            int32_t* status = P.status;
+            if constexpr (SEG) {
+                adopt(item);
+                const WalkSeg& g = P.seg[sh_seg[t]];
+                local = item - g.begin;
+                N = (unsigned long long)g.N;
+                p0 = (unsigned long long)g.p0;
+                st = g.stations;
+                status = g.status;
+            }
+            s = (uint32_t)(local / N);
+            p = (uint32_t)(p0 + local % N);
+            start = station_ok(P, st, status, s, item);
+        }
+        if (start) {
+            wx = (float)(st[3 * s + 0] - P.cen[0]);
+            wy = (float)(st[3 * s + 1] - P.cen[1]);
+            wz = (float)(st[3 * s + 2] - P.cen[2]);
             float r0, r1, r2;
-            rho3_f32<RHO>(P, wx, wy, wz, hf, r0, r1, r2);
+            rho3_f32<RHO>(P, M, wx, wy, wz, hf, r0, r1, r2);
             S0 = 0.5f * r0;
             S1 = 0.5f * r1;
             S2 = 0.5f * r2;
@@ -601,6 +657,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         const uint4* e = (const uint4*)(P.pool + slot * kPoolEntryBytes);
                         const uint4 e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3], e4 = e[4];
                         sh_item[t] = ((unsigned long long)e0.y << 32) | e0.x;
+                        adopt(sh_item[t]);
                         blk = e0.z;
                         alive = e0.w;
                         wx = __uint_as_float(e1.x);
@@ -661,7 +718,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
         for (int k = 0; k < 16; ++k) {
             if (busy) {
                 float z[12];
-                normals12_f32(s, p, blk, P.key0, P.key1, P.lnscale_f, z);
+                normals12_f32(s, p, blk, k0, k1, P.lnscale_f, z);
                 // Voxel grid: the block's four positions are known once its
                 // normals are, so all twelve density loads are issued here
                 // and their latency overlaps the steps (same positions, same
@@ -678,7 +735,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         px[m] = x;
                         py[m] = y;
                         pz[m] = zz;
-                        rho3_f32<RHO>(P, x, y, zz, hf, rv[m][0], rv[m][1], rv[m][2]);
+                        rho3_f32<RHO>(P, M, x, y, zz, hf, rv[m][0], rv[m][1], rv[m][2]);
                     }
                 }
 #pragma unroll
@@ -756,7 +813,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                             rb = rv[m][1];
                             rc = rv[m][2];
                         } else {
-                            rho3_f32<RHO>(P, nx, ny, nz, hf, ra, rb, rc);
+                            rho3_f32<RHO>(P, M, nx, ny, nz, hf, ra, rb, rc);
                         }
                         S0 += ra;
                         if (CRN) {
@@ -777,7 +834,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     busy = false;
                 } else if (4 * (int64_t)blk >= P.max_steps) {
                     const unsigned long long it = sh_item[t];
-                    atomicOr(P.status, 1 << MCG_ERR_STEP_CAP);
+                    atomicOr(SEG ? P.seg[sh_seg[t]].status : P.status, 1 << MCG_ERR_STEP_CAP);
                     P.drec[it] = no_record();  // copy 0 record marks "no result"
                     P.pp_steps[it] = sh_steps[t] + (long long)__popc(alive) * 4 * (long long)blk;
                     busy = false;
@@ -800,9 +857,16 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
 // Per-path values of one item from its exit records (double precision).  The
 // density at the last inside point is re-evaluated from X by the walk's own
 // single-precision function.
-template <int RHO>
+template <int RHO, bool SEG>
 __device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long long item, float hf)
 {
+    ModelRef M = model_of(P);
+    int32_t* status = P.status;
+    if constexpr (SEG) {  // the item's request: its model arrays and status word
+        const WalkSeg& g = P.seg[find_seg(P, item)];
+        M = model_of(g);
+        status = g.status;
+    }
     double u[3] = {kNaN, kNaN, kNaN};
     const int nc = P.crn ? 3 : 1;
     const size_t T = P.total;
@@ -810,15 +874,15 @@ __device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long lon
         const float* f = P.frec + (size_t)8 * c * T + item;
         const float xb = f[0], yb = f[T], zb = f[2 * T];
         float r[3];
-        rho3_f32<RHO>(P, xb, yb, zb, hf, r[0], r[1], r[2]);
+        rho3_f32<RHO>(P, M, xb, yb, zb, hf, r[0], r[1], r[2]);
         const float X[3] = {xb, yb, c == 0 ? zb : (c == 1 ? zb + hf : zb - hf)};
         const float Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
-        u[c] = exit_mixed(P, X, Y, P.drec[(size_t)c * T + item], f[6 * T], r[c]);
+        u[c] = exit_mixed(P, M, X, Y, P.drec[(size_t)c * T + item], f[6 * T], r[c]);
     }
     const double d = P.crn ? (u[1] - u[2]) / (2.0 * P.h) : kNaN;
     P.pp_u[item] = u[0];
     P.pp_d[item] = d;
-    if (!isfinite(u[0]) || (P.crn && !isfinite(d))) atomicOr(P.status, 1 << MCG_ERR_NONFINITE);
+    if (!isfinite(u[0]) || (P.crn && !isfinite(d))) atomicOr(status, 1 << MCG_ERR_NONFINITE);
 }
 
 // Exit evaluation, convergent: each warp scans its items 32 at a time, writes
@@ -826,7 +890,7 @@ __device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long lon
 // cancelled, never started, lost, outside Omega) and queues the others in
 // shared memory, evaluating them 32 at a time, so the slow double-precision
 // pipe never runs a warp whose lanes are mostly idle.
-template <int RHO>
+template <int RHO, bool SEG>
 __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
 {
     __shared__ unsigned long long queue[4][64];
@@ -851,7 +915,7 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
         qn += __popc(vm);
         __syncwarp();
         if (qn >= 32) {
-            exit_item<RHO>(P, q[lane], hf);
+            exit_item<RHO, SEG>(P, q[lane], hf);
             const int rest = qn - 32;
             unsigned long long v = 0ull;
             if (lane < rest) v = q[32 + lane];
@@ -861,13 +925,13 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
             qn = rest;
         }
     }
-    if (lane < qn) exit_item<RHO>(P, q[lane], hf);
+    if (lane < qn) exit_item<RHO, SEG>(P, q[lane], hf);
 }
 
-template <int RHO, bool CRN, bool BRIDGE, bool BALL>
+template <int RHO, bool CRN, bool BRIDGE, bool BALL, bool SEG>
 cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t st)
 {
-    walk_mixed_kernel<RHO, CRN, BRIDGE, BALL><<<grid, block, 0, st>>>(P);
+    walk_mixed_kernel<RHO, CRN, BRIDGE, BALL, SEG><<<grid, block, 0, st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -875,37 +939,45 @@ cudaError_t launch_mixed(const WalkParams& P, int block, int grid, cudaStream_t 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned long long need = (P.total + 127ull) / 128ull;
     const unsigned long long cap = (unsigned long long)sms * 16ull;
-    exit_mixed_kernel<RHO><<<(unsigned)(need < cap ? need : cap), 128, 0, st>>>(P);
+    exit_mixed_kernel<RHO, SEG><<<(unsigned)(need < cap ? need : cap), 128, 0, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int RHO>
 cudaError_t launch_mixed_rho(const WalkParams& P, int block, int grid, cudaStream_t st)
 {
-    if (P.ball) return P.crn ? launch_mixed<RHO, true, false, true>(P, block, grid, st)
-                             : launch_mixed<RHO, false, false, true>(P, block, grid, st);
-    if (P.crn) return P.bridge ? launch_mixed<RHO, true, true, false>(P, block, grid, st)
-                               : launch_mixed<RHO, true, false, false>(P, block, grid, st);
-    return P.bridge ? launch_mixed<RHO, false, true, false>(P, block, grid, st)
-                    : launch_mixed<RHO, false, false, false>(P, block, grid, st);
+    if (P.seg) return P.crn ? launch_mixed<RHO, true, false, false, true>(P, block, grid, st)
+                            : launch_mixed<RHO, false, false, false, true>(P, block, grid, st);
+    if (P.ball) return P.crn ? launch_mixed<RHO, true, false, true, false>(P, block, grid, st)
+                             : launch_mixed<RHO, false, false, true, false>(P, block, grid, st);
+    if (P.crn) return P.bridge ? launch_mixed<RHO, true, true, false, false>(P, block, grid, st)
+                               : launch_mixed<RHO, true, false, false, false>(P, block, grid, st);
+    return P.bridge ? launch_mixed<RHO, false, true, false, false>(P, block, grid, st)
+                    : launch_mixed<RHO, false, false, false, false>(P, block, grid, st);
 }
 
 template <int RHO>
-const void* mixed_fn(bool crn)
+const void* mixed_fn(bool crn, bool seg)
 {
-    return crn ? (const void*)walk_mixed_kernel<RHO, true, false, false>
-               : (const void*)walk_mixed_kernel<RHO, false, false, false>;
+    if (seg)
+        return crn ? (const void*)walk_mixed_kernel<RHO, true, false, false, true>
+                   : (const void*)walk_mixed_kernel<RHO, false, false, false, true>;
+    return crn ? (const void*)walk_mixed_kernel<RHO, true, false, false, false>
+               : (const void*)walk_mixed_kernel<RHO, false, false, false, false>;
 }
 
-const void* kernel_fn(int precision, int rho_kind, bool crn)
+const void* kernel_fn(int precision, int rho_kind, bool crn, bool seg)
 {
-    if (precision == MCG_FP64) return crn ? (const void*)walk_fp64_kernel<true> : (const void*)walk_fp64_kernel<false>;
+    if (precision == MCG_FP64) {
+        if (seg) return crn ? (const void*)walk_fp64_kernel<true, true> : (const void*)walk_fp64_kernel<false, true>;
+        return crn ? (const void*)walk_fp64_kernel<true, false> : (const void*)walk_fp64_kernel<false, false>;
+    }
     switch (rho_kind) {
-    case kRhoVoxelPacked: return mixed_fn<kRhoVoxelPacked>(crn);
-    case MCG_RHO_SPHERE: return mixed_fn<MCG_RHO_SPHERE>(crn);
-    case MCG_RHO_PRISM: return mixed_fn<MCG_RHO_PRISM>(crn);
-    case MCG_RHO_VOXEL: return mixed_fn<MCG_RHO_VOXEL>(crn);
-    default: return mixed_fn<MCG_RHO_NONE>(crn);
+    case kRhoVoxelPacked: return mixed_fn<kRhoVoxelPacked>(crn, seg);
+    case MCG_RHO_SPHERE: return mixed_fn<MCG_RHO_SPHERE>(crn, seg);
+    case MCG_RHO_PRISM: return mixed_fn<MCG_RHO_PRISM>(crn, seg);
+    case MCG_RHO_VOXEL: return mixed_fn<MCG_RHO_VOXEL>(crn, seg);
+    default: return mixed_fn<MCG_RHO_NONE>(crn, seg);
     }
 }
 
@@ -923,25 +995,26 @@ void touch(K kernel)
 template <int RHO>
 void touch_mixed()
 {
-    touch(walk_mixed_kernel<RHO, true, false, true>);
-    touch(walk_mixed_kernel<RHO, false, false, true>);
-    touch(walk_mixed_kernel<RHO, true, true, false>);
-    touch(walk_mixed_kernel<RHO, true, false, false>);
-    touch(walk_mixed_kernel<RHO, false, true, false>);
-    touch(walk_mixed_kernel<RHO, false, false, false>);
+    touch(walk_mixed_kernel<RHO, true, false, true, false>);
+    touch(walk_mixed_kernel<RHO, false, false, true, false>);
+    touch(walk_mixed_kernel<RHO, true, true, false, false>);
+    touch(walk_mixed_kernel<RHO, true, false, false, false>);
+    touch(walk_mixed_kernel<RHO, false, true, false, false>);
+    touch(walk_mixed_kernel<RHO, false, false, false, false>);
+    touch(walk_mixed_kernel<RHO, true, false, false, true>);
+    touch(walk_mixed_kernel<RHO, false, false, false, true>);
+    touch(exit_mixed_kernel<RHO, false>);
+    touch(exit_mixed_kernel<RHO, true>);
 }
 
 }  // namespace
 
 void preload_walk_kernels()
 {
-    touch(walk_fp64_kernel<true>);
-    touch(walk_fp64_kernel<false>);
-    touch(exit_mixed_kernel<MCG_RHO_NONE>);
-    touch(exit_mixed_kernel<MCG_RHO_SPHERE>);
-    touch(exit_mixed_kernel<MCG_RHO_PRISM>);
-    touch(exit_mixed_kernel<MCG_RHO_VOXEL>);
-    touch(exit_mixed_kernel<kRhoVoxelPacked>);
+    touch(walk_fp64_kernel<true, false>);
+    touch(walk_fp64_kernel<false, false>);
+    touch(walk_fp64_kernel<true, true>);
+    touch(walk_fp64_kernel<false, true>);
     touch_mixed<MCG_RHO_NONE>();
     touch_mixed<MCG_RHO_SPHERE>();
     touch_mixed<MCG_RHO_PRISM>();
@@ -949,10 +1022,10 @@ void preload_walk_kernels()
     touch_mixed<kRhoVoxelPacked>();
 }
 
-int walk_blocks_per_sm(int precision, int rho_kind, int block)
+int walk_blocks_per_sm(int precision, int rho_kind, int block, bool seg)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_fn(precision, rho_kind, true), block, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_fn(precision, rho_kind, true, seg), block, 0) !=
         cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
@@ -963,15 +1036,22 @@ cudaError_t launch_walk(const WalkParams& P, int precision, int block, cudaStrea
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // a multi-request launch runs in the box without the bridge test
+    if (P.seg && (P.ball || P.bridge || P.nseg <= 0)) return cudaErrorInvalidValue;
     const int kind = (P.rho_kind == MCG_RHO_VOXEL && P.zq) ? kRhoVoxelPacked : P.rho_kind;
-    const int per_sm = walk_blocks_per_sm(precision, kind, block);
+    const int per_sm = walk_blocks_per_sm(precision, kind, block, P.seg != nullptr);
     long long grid = (long long)sms * per_sm;
     const long long need = (long long)((P.total + (unsigned long long)block - 1ull) / (unsigned long long)block);
     if (grid > need) grid = need > 0 ? need : 1;
     const bool crn = P.crn != 0;
     if (precision == MCG_FP64) {
-        if (crn) walk_fp64_kernel<true><<<(int)grid, block, 0, st>>>(P);
-        else walk_fp64_kernel<false><<<(int)grid, block, 0, st>>>(P);
+        if (P.seg) {
+            if (crn) walk_fp64_kernel<true, true><<<(int)grid, block, 0, st>>>(P);
+            else walk_fp64_kernel<false, true><<<(int)grid, block, 0, st>>>(P);
+        } else {
+            if (crn) walk_fp64_kernel<true, false><<<(int)grid, block, 0, st>>>(P);
+            else walk_fp64_kernel<false, false><<<(int)grid, block, 0, st>>>(P);
+        }
         return cudaGetLastError();
     }
     switch (kind) {

@@ -60,7 +60,8 @@ class mcg_result(C.Structure):
 class mcg_server_config(C.Structure):
     _fields_ = [("streams", C.c_int32), ("max_active", C.c_int32), ("hbm_budget", C.c_int64),
                 ("chunk_paths", C.c_int64), ("min_paths", C.c_int64), ("max_paths", C.c_int64),
-                ("max_round_paths", C.c_int64), ("walk", mcg_options)]
+                ("max_round_paths", C.c_int64), ("walk", mcg_options), ("batch", C.c_int32),
+                ("batch_items", C.c_int64)]
 
 
 class mcg_station_state(C.Structure):
@@ -138,6 +139,8 @@ def load(path: str | None = None):
     lib.mcg_cancel.restype = C.c_int
     lib.mcg_request_info.argtypes = [vp, P(i64), P(i64), P(d)]
     lib.mcg_request_info.restype = C.c_int
+    lib.mcg_server_stats.argtypes = [vp, P(i64), P(i64)]
+    lib.mcg_server_stats.restype = C.c_int
     lib.mcg_request_free.argtypes = [vp]
     lib.mcg_request_free.restype = C.c_int
     lib.mcg_grf_work_bytes.argtypes = [i64, i64, i64]
@@ -425,6 +428,13 @@ def mcg_server_create(cfg: mcg_server_config) -> int:
     h = C.c_void_p()
     _check(load().mcg_server_create(C.byref(cfg), C.byref(h)))
     return h.value
+
+
+def mcg_server_stats(server: int):
+    """(walk launches, request rounds) of the server so far."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(load().mcg_server_stats(server, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def mcg_server_destroy(server: int) -> int:

@@ -41,7 +41,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "layout.c"
     structs = {"mcg_domain": M.mcg_domain, "mcg_density": M.mcg_density, "mcg_boundary": M.mcg_boundary,
-               "mcg_options": M.mcg_options, "mcg_result": M.mcg_result, "mcg_station_state": M.mcg_station_state}
+               "mcg_options": M.mcg_options, "mcg_result": M.mcg_result, "mcg_station_state": M.mcg_station_state,
+               "mcg_server_config": M.mcg_server_config}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcgrav.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')

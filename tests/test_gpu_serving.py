@@ -3,7 +3,9 @@ models and targets overlap on the GPU; each result must be the same alone and
 in the mix (bit for bit: a request's paths, chunks and merge order depend only
 on its own seed, stations and target), equal to the device-level solve with
 the same chunking, stop at its target, and honour cancellation and the HBM
-budget."""
+budget.  Rounds of compatible requests share walk launches (a segment table
+gives each walk its request's stations, seed and model arrays): the results
+equal those of a server that launches every round alone."""
 import time
 
 import numpy as np
@@ -34,9 +36,12 @@ def models():
     vox = W.voxel_survey(shape=(32, 32, 16), table_n=(33, 33))
     grid = oracle.grf_density(1, 32, 32, 16, sigma_vox=2.0, amp=300.0)
     faces = smooth_tables(vox, scale=-1e-4)
+    grid2 = oracle.grf_density(2, 32, 32, 16, sigma_vox=2.0, amp=300.0)   # same geometry, other grid
+    faces2 = smooth_tables(vox, seed=5, scale=-1e-4)
     m = {"sphere": (sph, M.mcg_model_create(M.problem(sph), sph.dt, sph.h)),
          "prism": (pri, M.mcg_model_create(M.problem(pri), pri.dt, pri.h)),
-         "voxel": (vox, M.mcg_model_create(M.problem(vox, grid=grid, faces=faces), vox.dt, vox.h))}
+         "voxel": (vox, M.mcg_model_create(M.problem(vox, grid=grid, faces=faces), vox.dt, vox.h)),
+         "voxel2": (vox, M.mcg_model_create(M.problem(vox, grid=grid2, faces=faces2), vox.dt, vox.h))}
     yield m
     for _, h in m.values():
         M.mcg_model_destroy(h)
@@ -149,3 +154,54 @@ def test_submit_validation(models):
             M.mcg_submit(sv, h, w.stations[:1], -1.0, 0)
     finally:
         M.mcg_server_destroy(sv)
+
+
+def _run_all(models, reqs, batch, **kw):
+    """All requests submitted at once; (results in order, (launches, rounds))."""
+    sph_w = models["sphere"][0]
+    cfg = M.server_config(M.options(sph_w), chunk_paths=CHUNK, min_paths=2 * CHUNK, max_paths=4 * CHUNK,
+                          batch=batch, **kw)
+    sv = M.mcg_server_create(cfg)
+    out = []
+    try:
+        hs = [M.mcg_submit(sv, models[name][1], st, target, seed) for name, st, target, seed in reqs]
+        for h, (name, st, _, _) in zip(hs, reqs):
+            rc, res = M.mcg_wait(h, len(st), 120_000)
+            assert rc == M.MCG_OK, (name, rc, M.last_error())
+            out.append(res)
+            M.mcg_request_free(h)
+        stats = M.mcg_server_stats(sv)
+    finally:
+        M.mcg_server_destroy(sv)
+    return out, stats
+
+
+def test_shared_launches_equal_separate_launches(models):
+    """Eight requests (sphere, prism and two voxel models of one geometry with
+    different grids and tables, different seeds, station sets and targets)
+    through a server that shares walk launches between compatible rounds and
+    through one that launches every round alone.  Sphere and prism results are
+    bit for bit the same; voxel results agree to the flush rounding of the
+    single-precision partial sums (which follows the warp schedule), with
+    identical path and step counts (their targets are out of reach, so both
+    servers stop them at max_paths).  A voxel walk read through the wrong
+    request's grid or tables would differ by far more."""
+    sw, pw, vw = models["sphere"][0], models["prism"][0], models["voxel"][0]
+    reqs = [("sphere", sw.stations[:3], 5e-3, 21), ("voxel", vw.stations[:9], 1e-9, 22),
+            ("sphere", sw.stations[3:8], 1e-2, 23), ("voxel2", vw.stations[100:104], 1e-9, 24),
+            ("prism", pw.stations[:2], 2e-2, 25), ("voxel", vw.stations[50:51], 1e-9, 26),
+            ("voxel2", vw.stations[7:20], 1e-9, 27), ("sphere", sw.stations[:1], 1e-2, 28)]
+    shared, (launches, rounds) = _run_all(models, reqs, 1, streams=2)
+    alone, (launches0, rounds0) = _run_all(models, reqs, 0, streams=2)
+    assert launches0 == rounds0
+    assert launches < rounds, (launches, rounds)       # rounds did share launches
+    for (name, _, _, _), a, b in zip(reqs, shared, alone):
+        for k in ("n_paths", "path_steps"):
+            assert np.array_equal(a[k], b[k]), (name, k)
+        if name.startswith("voxel"):
+            for k in ("u", "gz"):
+                np.testing.assert_allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.abs(b["u"]).max(),
+                                           err_msg=f"{name} {k}")
+        else:
+            for k in ("u", "gz", "se_u", "se_gz"):
+                assert np.array_equal(a[k], b[k]), (name, k)
