@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="threads per block of the walk (0: library default)")
     ap.add_argument("--migrate", type=int, default=1, choices=[0, 1],
                     help="hand the last walks of sparse warps to warps with free lanes (default 1)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="pick block, refill threshold and spill threshold with mcg_autotune first (default 1)")
     ap.add_argument("--cpu-paths", type=int, default=256, help="paths per station in the CPU-oracle sample")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
@@ -242,6 +244,14 @@ def run_ours(args):
     res = torch.empty((6, S), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     opts = [M.options(w, precision=M.MCG_MIXED, stream=s, block=args.block, migrate=args.migrate) for s in streams]
+    tuned = None
+    if args.autotune:
+        # the library's autotuner on this workload (stepping rate, then tail)
+        M.mcg_autotune(prob, stations, S, w.dt, w.seed, opts[0])
+        for o in opts[1:]:
+            o.block, o.refill_min, o.spill_max = opts[0].block, opts[0].refill_min, opts[0].spill_max
+        tuned = {"block": int(opts[0].block), "refill_min": int(opts[0].refill_min),
+                 "spill_max": int(opts[0].spill_max)}
 
     def path_block(j):
         # step j of this rank takes paths [p0, p0 + Bp) of every station: a
@@ -384,7 +394,8 @@ def run_ours(args):
                 "config": {"workload": "prism_ore_body", "stations": S, "paths_per_station_per_step": Bp,
                            "paths_per_station_total": total_paths, "step_m": 1.0, "h_m": 1.0,
                            "l2": "flushed: 256 MiB memset before every step",
-                           "parallelism": "path-sharded replicas" if world > 1 else "1 GPU"},
+                           "parallelism": "path-sharded replicas" if world > 1 else "1 GPU",
+                           "autotuned": tuned},
                 "stations_per_s_at_1e-3": stations_per_s, "paths_per_s": paths_per_s,
                 "mean_path_steps_per_path": mean_steps_per_path,
                 "rel_se_u_median": float(np.median(se_u / np.abs(u))),
@@ -743,6 +754,7 @@ def large_survey_block(M, W, steps, warmup, paths):
     ds = pair[0]
     M.mcg_autotune(ds.prob, ds.stations, ds.S, w.dt, w.seed, ds.opts)
     pair[1].opts.block, pair[1].opts.refill_min = ds.opts.block, ds.opts.refill_min
+    pair[1].opts.spill_max = ds.opts.spill_max
     pair[1].states = ds.states
 
     def run_steps(first, count):
@@ -815,7 +827,8 @@ def large_survey_block(M, W, steps, warmup, paths):
             "steps": steps, "warmup": warmup, "ms_per_step": t / steps * 1e3,
             "stations_per_s_at_1e-3": stations_per_s, "mean_path_steps_per_path": mean_steps,
             "median_paths_needed_at_1e-3": float(np.median(n_req)),
-            "autotuned": {"block": int(ds.opts.block), "refill_min": int(ds.opts.refill_min)},
+            "autotuned": {"block": int(ds.opts.block), "refill_min": int(ds.opts.refill_min),
+                          "spill_max": int(ds.opts.spill_max)},
             "fp64_walk": {"path_steps_per_s": rate64, "stations_per_s_at_1e-3": stations_per_s_64,
                           "how": "tail-free FP64 stepping rate (paths capped at 256 RNG-steps) on the same model"},
             "mixed_over_fp64_at_equal_se": stations_per_s / stations_per_s_64,

@@ -176,6 +176,10 @@ typedef struct {
                                 (about 0.1-1 s) for it, gives up, and the walk
                                 reports MCG_ERR_TIMEOUT; every real walk still
                                 finishes.  Needs the mixed walk with migrate = 1. */
+    int32_t spill_max;       /* mixed walk with migrate = 1: once the work list is used
+                                up, a warp with at most this many live walks (1..32,
+                                default 24; 0 = default) hands them to warps with free
+                                lanes (mcg_autotune picks it)                     */
 } mcg_options;
 
 /* Per-station outputs (caller-owned, length S; any pointer may be NULL). */
@@ -322,11 +326,17 @@ MCG_API int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double*
  *   parts[0 .. S-1]).  States with n = 0 are skipped.  Allocates nothing. */
 MCG_API int mcg_states_merge(const mcg_station_state* parts, int64_t R, int64_t S, mcg_station_state* out);
 
-/* mcg_autotune: picks opts->block (64, 96, 128) and opts->refill_min (1, 4,
- * 16) for this problem by timing short walks of the given stations (paths
- * capped at 2048 RNG-steps so every lane stays busy) and writes the fastest
- * pair into *opts.  stations_dev: DEVICE, S x 3.  Blocking; allocates and
- * frees a scratch area of mcg_walk's size for S x 2048 paths. */
+/* mcg_autotune: picks the launch shape of the walk for this problem and
+ * writes it into *opts, in two stages timed with CUDA events:
+ *   1. opts->block (64, 96, 128) and opts->refill_min (1, 4, 16) on short
+ *      walks of the given stations capped at 2048 RNG-steps (the stepping
+ *      rate, every lane busy);
+ *   2. mixed walk with migrate = 1: opts->spill_max (8, 16, 24, 32) on
+ *      uncapped walks, two per resident lane, whose launch ends in the
+ *      exit-time tail that walk migration shortens (skipped for the FP64
+ *      walk; stops early once one launch takes over 2 s).
+ * stations_dev: DEVICE, S x 3.  Blocking; allocates and frees a scratch
+ * area of mcg_walk's size for the larger of the two stages. */
 MCG_API int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
                          const double* stations_dev, int64_t S, double dt, uint64_t seed, mcg_options* opts);
 

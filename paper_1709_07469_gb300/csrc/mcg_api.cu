@@ -287,6 +287,8 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     if (P.bridge && P.ball) return set_error(MCG_ERR_ARG, "the Brownian-bridge test needs the box domain");
     if (o->refill_min < 0 || o->refill_min > 32) return set_error(MCG_ERR_ARG, "refill_min must be in [0, 32]");
     P.refill_min = o->refill_min > 0 ? o->refill_min : 1;
+    if (o->spill_max < 0 || o->spill_max > 32) return set_error(MCG_ERR_ARG, "spill_max must be in [0, 32]");
+    P.spill_max = o->spill_max > 0 ? o->spill_max : 24;
     P.bridge_k = -2.0 / (P.sd * P.sd);
     P.bridge_k_f = (float)P.bridge_k;
     // Conservative boxes for the walk's common step (all copies inside, no
@@ -432,6 +434,7 @@ void mcg_options_default(mcg_options* o)
     o->graph = 1;
     o->migrate = 1;
     o->fault_unpublished = 0;
+    o->spill_max = 24;
 }
 
 const char* mcg_last_error(void) { return g_err; }

@@ -45,6 +45,7 @@ struct WalkParams {
     double dt, sd, h, two_pi_G;
     float sd_f, h_f, lnscale_f;    // lnscale_f = -2 ln 2 sd^2
     int32_t crn, clip, bridge, refill_min;
+    int32_t spill_max;             // a warp with at most this many live walks hands them over
     float bridge_k_f;              // -2 / (sigma^2 dt), single precision
     double bridge_k;               // -2 / (sigma^2 dt)
     int64_t max_steps;

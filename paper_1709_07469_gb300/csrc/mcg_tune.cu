@@ -17,17 +17,29 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
     if (!opts || !stations_dev || S <= 0) return set_error(MCG_ERR_ARG, "autotune needs options and stations");
     WalkParams P;
     mcg_options o = *opts;
-    o.max_steps = 2048;  // every path runs exactly 2048 RNG-steps: no exit tail in the timing
+    o.max_steps = 2048;  // stage 1: every path runs exactly 2048 RNG-steps, no exit tail in the timing
     o.block = 128;
     o.refill_min = 1;
     int rc = make_params(domain, density, boundary, dt, seed, &o, P);
     if (rc) return rc;
-    // about 2.6e5 timed walks in all (a few per lane of the persistent grid),
-    // at most 2048 per station: enough to fill the GPU without a large scratch
-    int64_t N = (262144 + S - 1) / S;
-    if (N > 2048) N = 2048;
-    const size_t n = (size_t)S * (size_t)N;
-    const size_t work = mcg_walk_work_bytes(S, N, o.precision);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // Stage 1 (stepping rate): about 2.6e5 capped walks (a few per lane of the
+    // persistent grid), at most 2048 per station.  Stage 2 (exit-time tail):
+    // uncapped walks, two per resident lane, so the launch ends in the tail
+    // that migration shortens.
+    int64_t N1 = (262144 + S - 1) / S;
+    if (N1 > 2048) N1 = 2048;
+    const int kind = (P.rho_kind == MCG_RHO_VOXEL && P.zq) ? kRhoVoxelPacked : P.rho_kind;
+    const int64_t lanes = (int64_t)sms * walk_blocks_per_sm(o.precision, kind, 128) * 128;
+    int64_t N2 = (2 * lanes + S - 1) / S;
+    if ((double)N2 * (double)S > 1048576.0) N2 = (1048576 + S - 1) / S;
+    if (N2 < 1) N2 = 1;
+    const bool stage2 = o.precision == MCG_MIXED && o.migrate;
+    const int64_t Nmax = (stage2 && N2 > N1) ? N2 : N1;
+    const size_t n = (size_t)S * (size_t)Nmax;
+    const size_t work = mcg_walk_work_bytes(S, Nmax, o.precision);
     const size_t bytes = 3 * align256(n * sizeof(double)) + align256(work) + 256;
     char* buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, bytes);
@@ -35,41 +47,44 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
         cudaGetLastError();
         return set_error(MCG_ERR_OOM, "autotune scratch: %s", cudaGetErrorString(e));
     }
+    char* w = buf + 3 * align256(n * sizeof(double));
     P.stations = stations_dev;
     P.S = S;
-    P.N = N;
     P.p0 = 0;
-    P.total = (unsigned long long)n;
     P.pp_u = (double*)buf;
     P.pp_d = (double*)(buf + align256(n * sizeof(double)));
     P.pp_steps = (int64_t*)(buf + 2 * align256(n * sizeof(double)));
-    char* w = buf + 3 * align256(n * sizeof(double));
-    if (o.precision == MCG_MIXED) {
-        P.frec = (float*)w;
-        P.drec = (double*)(w + align256(n * 3 * 8 * sizeof(float)));
-    }
     P.status = (int32_t*)(w + align256(work));
     P.counter = (unsigned long long*)(w + align256(work) + 128);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
+    // times one launch of the current P (block threads) in ms, or < 0 on error
+    auto timed = [&](int block) -> float {
+        float ms = -1.0f;
+        if ((e = reset_walk(P, 0)) || (e = cudaEventRecord(a)) || (e = launch_walk(P, o.precision, block, 0)) ||
+            (e = cudaEventRecord(b)) || (e = cudaEventSynchronize(b)))
+            return -1.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    };
     const int blocks[3] = {64, 96, 128};
     const int refills[3] = {1, 4, 16};
     float best = 1e30f;
-    int best_block = 128, best_refill = 1;
+    int best_block = 128, best_refill = 1, best_spill = P.spill_max;
     rc = MCG_OK;
+    P.N = N1;
+    P.total = (unsigned long long)S * (unsigned long long)N1;
+    if (o.precision == MCG_MIXED) bind_work(P, w, false);
     for (int rep = 0; rep < 2 && rc == MCG_OK; ++rep) {  // the first pass warms up
         for (int bi = 0; bi < 3 && rc == MCG_OK; ++bi)
             for (int ri = 0; ri < 3 && rc == MCG_OK; ++ri) {
                 P.refill_min = refills[ri];
-                if ((e = cudaMemset(P.counter, 0, sizeof(unsigned long long))) || (e = cudaEventRecord(a)) ||
-                    (e = launch_walk(P, o.precision, blocks[bi], 0)) || (e = cudaEventRecord(b)) ||
-                    (e = cudaEventSynchronize(b))) {
+                const float ms = timed(blocks[bi]);
+                if (ms < 0.0f) {
                     rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
                     break;
                 }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, a, b);
                 if (rep == 1 && ms < best) {
                     best = ms;
                     best_block = blocks[bi];
@@ -77,12 +92,38 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
                 }
             }
     }
+    if (rc == MCG_OK && stage2) {
+        P.max_steps = opts->max_steps;
+        P.refill_min = best_refill;
+        P.N = N2;
+        P.total = (unsigned long long)S * (unsigned long long)N2;
+        bind_work(P, w, true);
+        const int spills[4] = {8, 16, 24, 32};
+        float best2 = 1e30f;
+        bool too_long = false;  // very long walks: keep the default
+        for (int rep = 0; rep < 2 && rc == MCG_OK && !too_long; ++rep)
+            for (int si = 0; si < 4 && rc == MCG_OK && !too_long; ++si) {
+                P.spill_max = spills[si];
+                const float ms = timed(best_block);
+                if (ms < 0.0f) {
+                    rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+                    break;
+                }
+                if (rep == 1 && ms < best2) {
+                    best2 = ms;
+                    best_spill = spills[si];
+                }
+                too_long = ms > 2000.0f;
+            }
+        if (too_long) best_spill = opts->spill_max > 0 ? opts->spill_max : 24;
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(buf);
     if (rc) return rc;
     opts->block = best_block;
     opts->refill_min = best_refill;
+    opts->spill_max = best_spill;
     return MCG_OK;
 }
 

@@ -105,7 +105,7 @@ __device__ __forceinline__ bool cancelled(const WalkParams& P)
 // Migration of walks between warps (mixed walk).  Once the work list is used
 // up, a warp's lanes empty one by one as its walks exit, and a warp with a
 // few long walks left would keep issuing instructions for 32 lanes to the
-// end.  Such a warp (at most kSpillMax walks live, migration on) writes its
+// end.  Such a warp (at most P.spill_max walks live, migration on) writes its
 // walks to the pool and leaves; warps with free lanes claim pooled walks.
 // A walk's state is all of it: the random streams are keyed by (station,
 // path, step), so where a walk continues does not change its numbers.
@@ -119,13 +119,9 @@ __device__ __forceinline__ bool cancelled(const WalkParams& P)
 //            and, if the pool still holds walks, takes them over.
 // Each warp spills at most once, so slots are never reused.
 // ---------------------------------------------------------------------------
-#ifndef MCG_SPILL_MAX
-#define MCG_SPILL_MAX 24
-#endif
 #ifndef MCG_SPILL_BACKLOG
 #define MCG_SPILL_BACKLOG 64
 #endif
-constexpr int kSpillMax = MCG_SPILL_MAX;               // spill a warp with at most this many walks
 constexpr unsigned long long kSpillBacklog = MCG_SPILL_BACKLOG;  // ... while fewer pooled walks wait
 constexpr int kReadySpin = 1 << 20;                   // bounded wait for a ready flag (~0.1 s)
 
@@ -678,7 +674,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             }
         }
         unsigned livem = __ballot_sync(kFull, busy);
-        if (migrate && !stop && !spilled && livem != 0u && __popc(livem) <= kSpillMax &&
+        if (migrate && !stop && !spilled && livem != 0u && __popc(livem) <= P.spill_max &&
             __any_sync(kFull, exhausted)) {
             // few walks left here and nothing new to start: hand them over
             unsigned long long base = 0ull;

@@ -49,7 +49,7 @@ class mcg_options(C.Structure):
                 ("crn_gz", C.c_int32), ("block", C.c_int32), ("max_steps", C.c_int64),
                 ("batch_paths", C.c_int64), ("stream", C.c_void_p), ("cancel", C.c_void_p),
                 ("bridge", C.c_int32), ("refill_min", C.c_int32), ("graph", C.c_int32),
-                ("migrate", C.c_int32), ("fault_unpublished", C.c_int32)]
+                ("migrate", C.c_int32), ("fault_unpublished", C.c_int32), ("spill_max", C.c_int32)]
 
 
 class mcg_result(C.Structure):

@@ -165,6 +165,7 @@ def test_autotune_picks_a_valid_launch_shape():
     ds = DeviceSolve(w, precision=M.MCG_MIXED)
     M.mcg_autotune(ds.prob, ds.stations, ds.S, w.dt, w.seed, ds.opts)
     assert ds.opts.block in (64, 96, 128) and ds.opts.refill_min in (1, 4, 16)
+    assert ds.opts.spill_max in (8, 16, 24, 32)
     r = ds.run()
     assert r["status"] == 0
 
