@@ -3,10 +3,12 @@
 //
 // One block per station reads the batch's per-path values twice: pass 1 the
 // mean, pass 2 the sum of squared deviations about it.  Each thread sums a
-// fixed strided subset with Neumaier compensation, then the block combines
-// the partials in a fixed pairwise tree, so the result does not depend on
-// scheduling.  The batch statistics are merged into the running state with
-// Chan's formula, batch after batch in the order the host issues them.
+// fixed strided subset with Neumaier compensation; the block then combines
+// the partials with warp shuffles (a butterfly over each warp's lanes, then
+// the same over the warps' sums), always in the same order, so the result
+// does not depend on scheduling.  The batch statistics are merged into the
+// running state with Chan's formula, batch after batch in the order the host
+// issues them.
 #include <cuda_runtime.h>
 
 #include "mcg_internal.h"
@@ -29,19 +31,24 @@ struct Neumaier {
     __device__ double value() const { return s + c; }
 };
 
-// Fixed-order pairwise sum of one double per thread; result in lane 0 of
-// the returned broadcast.
-__device__ double block_sum(double v, double* sh)
+// Block sum of one value per thread in a fixed order: a butterfly over the
+// lanes of each warp (__shfl_xor_sync: lanes i and i ^ o add the same two
+// numbers, so every lane ends with the same warp sum), then the same over the
+// warps' sums; every thread returns the block's sum.
+template <typename T>
+__device__ T block_sum(T v, T* sh)
 {
-    const int t = threadIdx.x;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    __syncthreads();  // the previous call's readers are done with sh
+    if (lane == 0) sh[w] = v;
     __syncthreads();
-    sh[t] = v;
-    __syncthreads();
-    for (int stride = kReduceThreads / 2; stride > 0; stride >>= 1) {
-        if (t < stride) sh[t] = sh[t] + sh[t + stride];
-        __syncthreads();
-    }
-    return sh[0];
+    T r = lane < kReduceThreads / 32 ? sh[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
+    return r;
 }
 
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __restrict__ pp_u,
@@ -49,8 +56,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
                                                                 const int64_t* __restrict__ pp_steps, int64_t N,
                                                                 mcg_station_state* __restrict__ states)
 {
-    __shared__ double sh[kReduceThreads];
-    __shared__ unsigned long long shs[kReduceThreads];
+    __shared__ double sh[kReduceThreads / 32];
+    __shared__ unsigned long long shs[kReduceThreads / 32];
     const int64_t s = blockIdx.x;
     const double* u = pp_u + s * N;
     const double* d = pp_d + s * N;
@@ -77,13 +84,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
     const double m2_u = block_sum(qu.value(), sh);
     const double m2_d = block_sum(qd.value(), sh);
 
-    __syncthreads();
-    shs[t] = steps;
-    __syncthreads();
-    for (int stride = kReduceThreads / 2; stride > 0; stride >>= 1) {
-        if (t < stride) shs[t] += shs[t + stride];
-        __syncthreads();
-    }
+    const unsigned long long steps_all = block_sum(steps, shs);
 
     if (t == 0) {
         mcg_station_state a = states[s];
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
             a.m2_d = a.m2_d + m2_d + dd * dd * (na * nb / n);
         }
         a.n = na + nb;
-        a.steps = a.steps + (double)shs[0];
+        a.steps = a.steps + (double)steps_all;
         states[s] = a;
     }
 }

@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             wy = (float)(st[3 * s + 1] - P.cen[1]);
             wz = (float)(st[3 * s + 2] - P.cen[2]);
             float r0, r1, r2;
-            rho3_f32<RHO>(P, M, wx, wy, wz, hf, r0, r1, r2);
+            rho3_f32<RHO>(P, SEG ? M : model_of(P), wx, wy, wz, hf, r0, r1, r2);
             S0 = 0.5f * r0;
             S1 = 0.5f * r1;
             S2 = 0.5f * r2;
@@ -714,12 +714,32 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
         for (int k = 0; k < 16; ++k) {
             if (busy) {
                 float z[12];
-                normals12_f32(s, p, blk, k0, k1, P.lnscale_f, z);
+                // (a single-request launch reads its key straight from the
+                // launch parameters: uniform across the warp)
+                normals12_f32(s, p, blk, SEG ? k0 : P.key0, SEG ? k1 : P.key1, P.lnscale_f, z);
                 // Voxel grid: the block's four positions are known once its
                 // normals are, so all twelve density loads are issued here
                 // and their latency overlaps the steps (same positions, same
                 // summation order: results are unchanged).
                 constexpr bool kPrefetch = RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked;
+                // common step: every copy surely inside Omega and surely
+                // outside the density's support -> nothing to do but move
+                auto common = [&](float nx, float ny, float nz, bool& inside_all, float& qxy) -> bool {
+                    qxy = BALL ? nx * nx + ny * ny : 0.0f;
+                    inside_all = BALL ? qxy + nz * nz < P.in_r2_f
+                                      : fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] && fabsf(nz) < P.in_f[2];
+                    bool no_rho = true;
+                    if constexpr (RHO == MCG_RHO_PRISM) {
+                        no_rho = !(fabsf(nx - P.far_c[0]) <= P.far_h[0] && fabsf(ny - P.far_c[1]) <= P.far_h[1] &&
+                                   fabsf(nz - P.far_c[2]) <= P.far_h[2]);
+                    } else if constexpr (RHO == MCG_RHO_SPHERE) {
+                        const float dx = nx - P.sc_f[0], dy = ny - P.sc_f[1], dz = nz - P.sc_f[2];
+                        no_rho = dx * dx + dy * dy + dz * dz > P.far_r2;
+                    } else if constexpr (RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked) {
+                        no_rho = false;
+                    }
+                    return inside_all && no_rho;
+                };
                 float px[4], py[4], pz[4], rv[4][3];
                 if constexpr (kPrefetch) {
                     float x = wx, y = wy, zz = wz;
@@ -731,7 +751,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         px[m] = x;
                         py[m] = y;
                         pz[m] = zz;
-                        rho3_f32<RHO>(P, M, x, y, zz, hf, rv[m][0], rv[m][1], rv[m][2]);
+                        rho3_f32<RHO>(P, SEG ? M : model_of(P), x, y, zz, hf, rv[m][0], rv[m][1], rv[m][2]);
                     }
                 }
 #pragma unroll
@@ -739,23 +759,9 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     const float nx = kPrefetch ? px[m] : wx + z[3 * m];
                     const float ny = kPrefetch ? py[m] : wy + z[3 * m + 1];
                     const float nz = kPrefetch ? pz[m] : wz + z[3 * m + 2];
-                    // common step: every copy surely inside Omega and surely
-                    // outside the density's support -> nothing to do but move
-                    const float qxy = BALL ? nx * nx + ny * ny : 0.0f;
-                    const bool inside_all = BALL ? qxy + nz * nz < P.in_r2_f
-                                                 : fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] &&
-                                                       fabsf(nz) < P.in_f[2];
-                    bool no_rho = true;
-                    if constexpr (RHO == MCG_RHO_PRISM) {
-                        no_rho = !(fabsf(nx - P.far_c[0]) <= P.far_h[0] && fabsf(ny - P.far_c[1]) <= P.far_h[1] &&
-                                   fabsf(nz - P.far_c[2]) <= P.far_h[2]);
-                    } else if constexpr (RHO == MCG_RHO_SPHERE) {
-                        const float dx = nx - P.sc_f[0], dy = ny - P.sc_f[1], dz = nz - P.sc_f[2];
-                        no_rho = dx * dx + dy * dy + dz * dz > P.far_r2;
-                    } else if constexpr (RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked) {
-                        no_rho = false;
-                    }
-                    if (!(inside_all && no_rho)) {  // otherwise rho = 0 at every copy: sums unchanged
+                    bool inside_all;
+                    float qxy;
+                    if (!common(nx, ny, nz, inside_all, qxy)) {  // otherwise rho = 0 at every copy: sums unchanged
                         if (!inside_all) {
                             unsigned ins;
                             if (BALL) {
@@ -809,7 +815,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                             rb = rv[m][1];
                             rc = rv[m][2];
                         } else {
-                            rho3_f32<RHO>(P, M, nx, ny, nz, hf, ra, rb, rc);
+                            rho3_f32<RHO>(P, SEG ? M : model_of(P), nx, ny, nz, hf, ra, rb, rc);
                         }
                         S0 += ra;
                         if (CRN) {

@@ -113,3 +113,36 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             M.load(str(tmp_path / "missing.so"))
     finally:
         M._lib = saved
+
+
+def test_new_entry_points_check_arguments_without_gpu(lib):
+    """Host-side checks of the packed-array, exact-field, probe and server
+    entry points answer before any launch."""
+    assert M.mcg_voxel_pack_bytes(128, 128, 64) == 16 * 128 * 128 * 66
+    assert M.mcg_voxel_pack_bytes(0, 1, 1) == 0
+    assert M.mcg_table_pack_bytes(256, 256) == 16 * 6 * 255 * 255
+    assert M.mcg_table_pack_bytes(1, 5) == 0
+    w = W.voxel_survey(shape=(4, 4, 2), table_n=(3, 3)).with_(g_kind="zero")
+    grid = np.zeros((2, 4, 4), dtype=np.float32)
+    prob = M.problem(w, grid=grid)
+    with pytest.raises(M.McgError):                       # 16-byte alignment of the output
+        M.mcg_voxel_pack(prob, grid.ctypes.data + 4)
+    sph = M.problem(W.sphere_line())
+    with pytest.raises(M.McgError):                       # not a voxel density
+        M.mcg_voxel_pack(sph, grid.ctypes.data)
+    assert M.mcg_field(sph, None, 0) == M.MCG_OK
+    with pytest.raises(M.McgError):
+        M.mcg_field(sph, None, -1, grid.ctypes.data)
+    with pytest.raises(M.McgError):
+        M.mcg_issue_probe(7)
+    c = M.server_config()
+    assert c.batch == 1 and c.batch_items == 1 << 22 and c.walk.spill_max == 24
+    assert c.walk.fault_unpublished == 0
+
+
+def test_walk_option_ranges_without_gpu(lib):
+    w = W.sphere_line(paths=10)
+    assert _solve_status(w, fault_unpublished=256) == M.MCG_ERR_ARG
+    assert "fault_unpublished" in M.last_error()
+    assert _solve_status(w, spill_max=33) == M.MCG_ERR_ARG
+    assert "spill_max" in M.last_error()
