@@ -296,7 +296,7 @@ __device__ __forceinline__ double exit_mixed(const WalkParams& P, const ModelRef
     const double r = rho_f64(P, M, xs);
     const double rpd = (double)rp;
     const double I = P.dt * (acc - 0.5 * rpd) + 0.5 * theta * P.dt * (rpd + r);
-    return boundary_value(P, M, face, xs) - P.two_pi_G * I;
+    return boundary_value<true>(P, M, face, xs) - P.two_pi_G * I;
 }
 
 // Exit records of the mixed walk (structure of arrays, item-major):
