@@ -385,7 +385,7 @@ def run_ours(args):
                                                    "sample": f"{S} stations x {n1} paths, 1 thread, {dt1:.1f} s"}}
             out["accuracy"]["vs_fp64_oracle"] = paired_with_oracle(M, w, ref, args.cpu_paths, dev)
         if not args.skip_survey and world == 1:
-            out["large_survey"] = large_survey_block(M, W, steps=3, warmup=1, paths=args.survey_paths)
+            out["large_survey"] = large_survey_block(M, W, steps=6, warmup=1, paths=args.survey_paths)
         if not args.skip_serving and world == 1:
             out["serving"] = serving_block(M, W, args)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
