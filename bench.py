@@ -45,6 +45,13 @@ SM_MAX_MHZ = 2070.0   # used when nvidia-smi reports no maximum SM clock
 # density 13 + trapezoid 3 = 74; per path-step (3 copies) 74 / 3.
 OPS_PER_RNG_STEP = 74.0
 OPS_PER_PATH_STEP = OPS_PER_RNG_STEP / 3.0
+# Double-precision FMA / add / multiply thread-instructions of the plain FP64
+# walk per RNG-step (its Box-Muller transform, step, tests and sums in
+# double precision), counted by ncu (smsp__sass_thread_inst_executed_op_
+# {dfma,dadd,dmul}_pred_on.sum) on 30 x 32768 prism paths capped at 64
+# RNG-steps; the FP64 walk's roofline is this count against the measured DFMA
+# rate.
+FP64_OPS_PER_RNG_STEP = 118.8
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one walk_mixed_kernel launch per work item,
 # from ncu's dram__bytes_read.sum + dram__bytes_write.sum on 30 x 8192 items of
@@ -370,6 +377,7 @@ def run_ours(args):
             out["accuracy"] = accuracy_vs_closed_form(M, w, r, dev)
         if not args.skip_fp64 and world == 1:
             out["fp64_walk"] = fp64_comparison(M, w, dev)
+            out["fp64_walk"]["roofline"] = fp64_roofline(M, out["fp64_walk"]["fp64"]["path_steps_per_s"])
             out["fp64_walk"].update(fp64_at_equal_se(M, w, dev, out["fp64_walk"], mean_steps_per_path,
                                                      float(np.mean(n_req)), args.fp64_batch, args.fp64_steps))
         if not args.skip_e2e and world == 1:
@@ -435,6 +443,20 @@ def measured_peaks(M, achieved):
         out[name] = {"tlane_op_per_s": rate / 1e12, "probe_s": secs, "frac": achieved / (rate / 1e12)}
     out["how"] = "8 independent chains per thread, every SM, CUDA events after a warm-up launch"
     return out
+
+
+def fp64_roofline(M, path_steps_per_s):
+    """The plain FP64 walk against the GPU's measured DFMA rate (probe kind
+    2): its double-precision FMA / add / multiply instructions per second over
+    the rate the FP64 pipe sustains on independent DFMAs.  Capped paths keep
+    all three copies alive, so RNG-steps = path-steps / 3."""
+    rate, secs = M.mcg_issue_probe(2, 256)
+    achieved = path_steps_per_s / 3.0 * FP64_OPS_PER_RNG_STEP / 1e12
+    return {"bound": "fp64", "achieved": achieved, "peak": rate / 1e12, "unit": "Tlane-op/s",
+            "frac": achieved / (rate / 1e12), "ops_per_rng_step": FP64_OPS_PER_RNG_STEP, "probe_s": secs,
+            "kernel": "walk_fp64_kernel<crn>",
+            "peak_source": "measured: 8 independent DFMA chains per thread on every SM, CUDA events",
+            "ops_source": "ncu DFMA + DADD + DMUL thread-instructions per RNG-step on the capped prism case"}
 
 
 def accuracy_vs_closed_form(M, w, r, dev):

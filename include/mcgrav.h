@@ -333,8 +333,10 @@ MCG_API int mcg_states_merge(const mcg_station_state* parts, int64_t R, int64_t 
  *      rate, every lane busy);
  *   2. mixed walk with migrate = 1: opts->spill_max (8, 16, 24, 32) on
  *      uncapped walks, two per resident lane, whose launch ends in the
- *      exit-time tail that walk migration shortens (skipped for the FP64
- *      walk; stops early once one launch takes over 2 s).
+ *      exit-time tail that walk migration shortens: the median of three
+ *      timed launches per value, and the incoming value (24 when unset)
+ *      stays unless another is more than 1 % faster (skipped for the FP64
+ *      walk; stops early, keeping it, once one launch takes over 2 s).
  * stations_dev: DEVICE, S x 3.  Blocking; allocates and frees a scratch
  * area of mcg_walk's size for the larger of the two stages. */
 MCG_API int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
@@ -551,10 +553,12 @@ MCG_API int mcg_field(const mcg_density* density, const double* points_dev, int6
 /* ---------------------------------------------------------------------- */
 
 /* mcg_issue_probe: the lane-instruction rate the current GPU sustains on long
- * runs of independent single-precision FMAs (kind 0) or of FMAs and
- * three-input xors side by side (kind 1, the two pipes the walk's generator
- * and transform use), one persistent launch over every SM, timed with CUDA
- * events after a warm-up launch.  No counterpart in the paper: it measures
+ * runs of independent single-precision FMAs (kind 0), of FMAs and three-input
+ * xors side by side (kind 1, the two pipes the mixed walk's generator and
+ * transform use) or of double-precision FMAs (kind 2, the pipe the plain
+ * FP64 walk is bound by), one persistent launch over every SM, timed with
+ * CUDA events after a warm-up launch.  Any other kind: MCG_ERR_ARG before any
+ * CUDA call.  No counterpart in the paper: it measures
  * the hardware the walk runs on.  lane_ops_per_s, seconds: HOST (either may
  * be NULL).  Blocking; allocates and frees 4 bytes of device memory. */
 MCG_API int mcg_issue_probe(int32_t kind, int32_t iters, double* lane_ops_per_s, double* seconds);

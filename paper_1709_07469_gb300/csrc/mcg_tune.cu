@@ -98,10 +98,15 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
         P.N = N2;
         P.total = (unsigned long long)S * (unsigned long long)N2;
         bind_work(P, w, true);
+        // A launch of uncapped walks ends in its longest walks, so one timing
+        // per candidate is noisy: the median of three timed launches (after
+        // one warm-up pass) decides, and the default threshold stays unless
+        // another is faster by more than 1 %.
         const int spills[4] = {8, 16, 24, 32};
-        float best2 = 1e30f;
+        const int dflt = P.spill_max;
+        float t[4][3];
         bool too_long = false;  // very long walks: keep the default
-        for (int rep = 0; rep < 2 && rc == MCG_OK && !too_long; ++rep)
+        for (int rep = 0; rep < 4 && rc == MCG_OK && !too_long; ++rep)
             for (int si = 0; si < 4 && rc == MCG_OK && !too_long; ++si) {
                 P.spill_max = spills[si];
                 const float ms = timed(best_block);
@@ -109,12 +114,24 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
                     rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
                     break;
                 }
-                if (rep == 1 && ms < best2) {
-                    best2 = ms;
-                    best_spill = spills[si];
-                }
+                if (rep > 0) t[si][rep - 1] = ms;
                 too_long = ms > 2000.0f;
             }
+        if (rc == MCG_OK && !too_long) {
+            float med[4], med_dflt = -1.0f;
+            for (int si = 0; si < 4; ++si) {
+                const float a = t[si][0], b = t[si][1], c = t[si][2];
+                med[si] = a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
+                if (spills[si] == dflt) med_dflt = med[si];
+            }
+            float best2 = med_dflt > 0.0f ? med_dflt / 1.01f : 1e30f;
+            best_spill = dflt;
+            for (int si = 0; si < 4; ++si)
+                if (med[si] < best2) {
+                    best2 = med[si];
+                    best_spill = spills[si];
+                }
+        }
         if (too_long) best_spill = opts->spill_max > 0 ? opts->spill_max : 24;
     }
     cudaEventDestroy(a);

@@ -133,8 +133,9 @@ def test_new_entry_points_check_arguments_without_gpu(lib):
     assert M.mcg_field(sph, None, 0) == M.MCG_OK
     with pytest.raises(M.McgError):
         M.mcg_field(sph, None, -1, grid.ctypes.data)
-    with pytest.raises(M.McgError):
-        M.mcg_issue_probe(7)
+    for kind in (-1, 3, 7):
+        with pytest.raises(M.McgError):
+            M.mcg_issue_probe(kind)
     c = M.server_config()
     assert c.batch == 1 and c.batch_items == 1 << 22 and c.walk.spill_max == 24
     assert c.walk.fault_unpublished == 0
@@ -146,3 +147,17 @@ def test_walk_option_ranges_without_gpu(lib):
     assert "fault_unpublished" in M.last_error()
     assert _solve_status(w, spill_max=33) == M.MCG_ERR_ARG
     assert "spill_max" in M.last_error()
+
+
+def test_walk_index_limits_without_gpu(lib):
+    """Path indices are the 32-bit counter word p: p0 + N may reach 2^32 but
+    not pass it; checked before any device pointer is touched."""
+    w = W.sphere_line(paths=10)
+    prob = M.problem(w)
+    opts = M.options(w)
+    fake = 0x1000  # never dereferenced: the checks fail first
+    for p0, N in ((2**32 - 10, 11), (2**32, 1), (-1, 5)):
+        rc = lib.mcg_walk(C.byref(prob.domain), C.byref(prob.density), C.byref(prob.boundary), fake, 8, p0, N,
+                          w.dt, 0, C.byref(opts), fake, fake, fake, fake, fake, fake)
+        assert rc == M.MCG_ERR_ARG, (p0, N)
+        assert ("non-negative" if p0 < 0 else "32 bits") in M.last_error()

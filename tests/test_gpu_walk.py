@@ -66,13 +66,54 @@ def test_fp64_per_path_sphere_line_full():
     assert flips < 1e-4, flips
 
 
+def prism_rounding_bound(w, x, ulps=16):
+    """Error bound of the prism's closed form at x from the rounding of its
+    terms: `ulps` units of roundoff of the absolute sum of the 48 terms of
+    Nagy's corner sum (Sec. 4.2), times G rho.  At exit points on the domain's
+    faces that sum is up to ~3e4 |u|, so two correct evaluations that differ
+    only in their log / atan implementations (CUDA's and the host's libm) or
+    in fused multiply-adds differ by far more than 1e-12 |u|."""
+    tot = 0.0
+    for c in range(8):
+        X, Y, Z = [(w.phi[k] if (c >> k) & 1 else w.plo[k]) - x[k] for k in range(3)]
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        for a, b, q in ((X, Y, Z), (Y, Z, X), (Z, X, Y)):
+            if a * b != 0.0:  # ln(q + r), q + r = (a^2 + b^2) / (r - q) for q < 0
+                ln = np.log(q + r) if q >= 0.0 else np.log(a * a + b * b) - np.log(r - q)
+                tot += abs(a * b * ln)
+            if a != 0.0:
+                tot += abs(0.5 * a * a * np.arctan(b * q / (a * r)))
+    return ulps * np.finfo(np.float64).eps * abs(w.G * w.rho0) * tot
+
+
 def test_fp64_per_path_prism_sampled_paths():
     """Prism ore body (step 1 m, ~1.4e5 RNG-steps per path): all 30 stations x
     16 paths at the highest path indices of the full 10^6-path configuration
-    (480 walks; the bench line checks paths 0-255 of every station)."""
+    (480 walks; the bench line checks paths 0-255 of every station).  Where
+    the exit steps agree, u and d agree to 1e-12 |u| plus the closed form's
+    own rounding bound at the copies' exit points."""
     w = W.prism_ore_body()
-    flips, n = compare_fp64(w, 16, p0=999_984)
-    assert flips * n <= 1.0 + 1e-9, flips * n
+    N, p0 = 16, 999_984
+    u, d, steps, status = gpu_per_path(w, M.MCG_FP64, N, p0=p0)
+    assert status == 0
+    spec = oracle_spec(w)
+    flips, worst = 0, 0.0
+    for s in range(w.n_stations):
+        for j in range(N):
+            rc, uc, st, xe = oracle.walk_path(spec, w.stations[s], s, p0 + j)
+            assert rc == 0
+            if st.sum() != steps[s, j]:
+                flips += 1
+                continue
+            b = [prism_rounding_bound(w, xe[c]) for c in range(3)]
+            tol_u = 1e-12 * abs(uc[0]) + b[0]
+            tol_d = (2e-12 * abs(uc[0]) + b[1] + b[2]) / (2.0 * w.h)
+            err_u = abs(u[s, j] - uc[0])
+            err_d = abs(d[s, j] - (uc[1] - uc[2]) / (2.0 * w.h))
+            assert err_u <= tol_u and err_d <= tol_d, (s, j, err_u, tol_u, err_d, tol_d)
+            worst = max(worst, err_u / abs(uc[0]))
+    print(f"max relative |u - oracle| over matched paths: {worst:.3e}; flips {flips} of {w.n_stations * N}")
+    assert flips <= 1
 
 
 @pytest.mark.parametrize("name,poly", [("linear", (0.3, 1.0, 2.0, -1.0, 0, 0, 0, 0, 0, 0, 0)),
@@ -420,3 +461,28 @@ def test_prism_full_size_launch_sampled_paths_mixed():
             rel.append(abs(u[s, j] - uc[0]) / abs(uc[0]))
     assert np.mean(same) > 0.8
     assert np.median(rel) < 1e-5
+
+
+def test_largest_path_indices_and_seed():
+    """The last 40 path indices a launch may use (p0 + N = 2^32) under the
+    all-ones seed (key words 0xFFFFFFFF): the FP64 walk equals the oracle path
+    by path, and the mixed walk follows the oracle's 23-bit-uniform walk of
+    the same indices (same exit step for most paths, u to single-precision
+    rounding where it does)."""
+    w = W.sphere_line().with_(seed=2**64 - 1)
+    N, p0 = 40, 2**32 - 40
+    flips, n = compare_fp64(w, N, p0=p0)
+    assert flips * n <= 1.0 + 1e-9, flips * n
+    u, d, steps, status = gpu_per_path(w, M.MCG_MIXED, N, p0=p0)
+    assert status == 0
+    spec = oracle_spec(w, ubits=23)
+    same, rel = [], []
+    for s in range(w.n_stations):
+        for j in range(N):
+            rc, uc, st, _ = oracle.walk_path(spec, w.stations[s], s, p0 + j)
+            assert rc == 0
+            same.append(st.sum() == steps[s, j])
+            if same[-1]:
+                rel.append(abs(u[s, j] - uc[0]) / abs(uc[0]))
+    assert np.mean(same) > 0.8
+    assert np.median(rel) < 1e-4
