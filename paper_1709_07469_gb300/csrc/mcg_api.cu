@@ -274,10 +274,11 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
     P.two_pi_G = 2.0 * kPi * R->G;
     P.sd_f = (float)P.sd;
     P.h_f = (float)P.h;
+    if (R->kind == MCG_RHO_VOXEL) P.hz_f = (float)(P.h / R->spacing[2]);
     if (R->kind == MCG_RHO_VOXEL && R->zpack) {
         if ((uintptr_t)R->zpack % 16 != 0) return set_error(MCG_ERR_ARG, "voxel zpack must be 16-byte aligned");
         // one packed entry covers the copies' layers only while h <= half a cell
-        if (!(P.h_f * P.inv_sp_f[2] <= 0.5f)) return set_error(MCG_ERR_ARG, "zpack needs h <= spacing[2] / 2");
+        if (!(P.hz_f <= 0.5f)) return set_error(MCG_ERR_ARG, "zpack needs h <= spacing[2] / 2");
         P.zq = (const float4*)R->zpack;
     }
     P.lnscale_f = (float)(-2.0 * std::log(2.0) * P.sd * P.sd);
@@ -550,7 +551,7 @@ int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, const mcg
     if (bnd.kind == MCG_G_TABLE && bnd.faces && host_memory(bnd.faces))
         faces_bytes = 6 * (size_t)bnd.nu * (size_t)bnd.nv * sizeof(float);
     // packed copies for the walk's 16-byte loads, unless the caller brought them
-    if (den.kind == MCG_RHO_VOXEL && !den.zpack && P.h_f * P.inv_sp_f[2] <= 0.5f)
+    if (den.kind == MCG_RHO_VOXEL && !den.zpack && P.hz_f <= 0.5f)
         zpack_bytes = mcg_voxel_pack_bytes(den.nx, den.ny, den.nz);
     if (bnd.kind == MCG_G_TABLE && !bnd.quads) quad_bytes = mcg_table_pack_bytes(bnd.nu, bnd.nv);
     const size_t bytes = solve_shared_bytes(S) + (size_t)nsets * set_bytes + align256(grid_bytes) +

@@ -159,6 +159,36 @@ __device__ __forceinline__ int find_seg(const WalkParams& P, unsigned long long 
 // ---------------------------------------------------------------------------
 // Density samplers.
 // ---------------------------------------------------------------------------
+// floor(t) as an integer without a conversion instruction: adding
+// 1.5 * 2^23 rounded toward -infinity leaves floor(t) + 1.5 * 2^23 exactly
+// for |t| < 2^22 (the float spacing there is 1), so its bit pattern minus
+// that of 1.5 * 2^23 is floor(t).  Beyond |t| >= 2^22 the result is far
+// outside any grid (below -2^22 or at least 2^22), which the callers' range
+// tests reject.
+constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr uint32_t kFloorMagicBits = 0x4B400000u;
+
+__device__ __forceinline__ int floor_int(float t)
+{
+    return (int)(__float_as_uint(__fadd_rd(t, kFloorMagic)) - kFloorMagicBits);
+}
+
+// Cell of a point of the voxel grid: t_k = (x_k - origin_k) / spacing_k in
+// single precision (difference, then product with the reciprocal spacing),
+// cell index floor(t_k); for z also the position within the layer,
+// fr = t_z - floor(t_z) (exact: Sterbenz, or t_z itself below 1), which
+// places the copies at z +- h.
+__device__ __forceinline__ void voxel_cell(const WalkParams& P, float x, float y, float z, int& ix, int& iy, int& iz,
+                                           float& fr)
+{
+    ix = floor_int(__fmul_rn(__fsub_rn(x, P.org_f[0]), P.inv_sp_f[0]));
+    iy = floor_int(__fmul_rn(__fsub_rn(y, P.org_f[1]), P.inv_sp_f[1]));
+    const float tz = __fmul_rn(__fsub_rn(z, P.org_f[2]), P.inv_sp_f[2]);
+    const float vz = __fadd_rd(tz, kFloorMagic);
+    iz = (int)(__float_as_uint(vz) - kFloorMagicBits);
+    fr = __fsub_rn(tz, __fsub_rn(vz, kFloorMagic));
+}
+
 // Density at the three common-random-number copies (x, y, z), (x, y, z+h),
 // (x, y, z-h): the x / y part is computed once.  Every rounding step is
 // explicit (no contraction left to the compiler), so the walk kernel and the
@@ -182,34 +212,38 @@ __device__ __forceinline__ void rho3_f32(const WalkParams& P, const ModelRef& M,
         rb = (inxy && zb >= P.plo_f[2] && zb < P.phi_f[2]) ? P.rho0_f : 0.0f;
         rc = (inxy && zc >= P.plo_f[2] && zc < P.phi_f[2]) ? P.rho0_f : 0.0f;
     } else if constexpr (RHO == MCG_RHO_VOXEL) {
-        const float tx = floorf(__fmul_rn(__fsub_rn(x, P.org_f[0]), P.inv_sp_f[0]));
-        const float ty = floorf(__fmul_rn(__fsub_rn(y, P.org_f[1]), P.inv_sp_f[1]));
-        const bool inxy = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny;
-        const int base = (int)tx + P.nx * (int)ty;
-        const float za = floorf(__fmul_rn(__fsub_rn(z, P.org_f[2]), P.inv_sp_f[2]));
-        const float zb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
-        const float zc = floorf(__fmul_rn(__fsub_rn(__fsub_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
-        const int plane = P.nx * P.ny;
-        ra = (inxy && za >= 0.f && za < (float)P.nz) ? __ldg(M.grid + base + plane * (int)za) : 0.0f;
-        rb = (inxy && zb >= 0.f && zb < (float)P.nz) ? __ldg(M.grid + base + plane * (int)zb) : 0.0f;
-        rc = (inxy && zc >= 0.f && zc < (float)P.nz) ? __ldg(M.grid + base + plane * (int)zc) : 0.0f;
+        int ix, iy, iz;
+        float fr;
+        voxel_cell(P, x, y, z, ix, iy, iz, fr);
+        // unsigned index arithmetic: out-of-range cells wrap to large values
+        // that the range tests reject (no signed overflow)
+        const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, nz = (unsigned)P.nz;
+        const bool inxy = (unsigned)ix < nx && (unsigned)iy < ny;
+        const unsigned base = (unsigned)ix + nx * (unsigned)iy, plane = nx * ny;
+        // the copies' layers: iz + floor(fr + h / dz), iz + floor(fr - h / dz)
+        const unsigned ka = (unsigned)iz;
+        const unsigned kb = ka + (unsigned)floor_int(__fadd_rn(fr, P.hz_f));
+        const unsigned kc = ka + (unsigned)floor_int(__fsub_rn(fr, P.hz_f));
+        ra = (inxy && ka < nz) ? __ldg(M.grid + (base + plane * ka)) : 0.0f;
+        rb = (inxy && kb < nz) ? __ldg(M.grid + (base + plane * kb)) : 0.0f;
+        rc = (inxy && kc < nz) ? __ldg(M.grid + (base + plane * kc)) : 0.0f;
     } else if constexpr (RHO == kRhoVoxelPacked) {
-        // The same cells as above, read through the packed grid: the copies'
-        // layers zb, zc differ from za by at most one (h <= half a cell), and
-        // the 16-byte entry of layer za holds layers za-1, za, za+1 (0 outside
-        // the grid), so one load serves all three copies.
-        const float tx = floorf(__fmul_rn(__fsub_rn(x, P.org_f[0]), P.inv_sp_f[0]));
-        const float ty = floorf(__fmul_rn(__fsub_rn(y, P.org_f[1]), P.inv_sp_f[1]));
-        const float za = floorf(__fmul_rn(__fsub_rn(z, P.org_f[2]), P.inv_sp_f[2]));
-        const float zb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
-        const float zc = floorf(__fmul_rn(__fsub_rn(__fsub_rn(z, h), P.org_f[2]), P.inv_sp_f[2]));
-        const bool in = tx >= 0.f && tx < (float)P.nx && ty >= 0.f && ty < (float)P.ny && za >= -1.f &&
-                        za <= (float)P.nz;
+        // The same cells as above, read through the packed grid: with
+        // h <= half a cell the copies' layers differ from iz by at most one
+        // (floor(fr + h/dz) is 1 exactly when the rounded sum reaches 1, and
+        // floor(fr - h/dz) is -1 exactly when fr < h/dz), and the 16-byte
+        // entry of layer iz holds layers iz-1, iz, iz+1 (0 outside the grid),
+        // so one load serves all three copies.
+        int ix, iy, iz;
+        float fr;
+        voxel_cell(P, x, y, z, ix, iy, iz, fr);
+        const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, kz = (unsigned)iz + 1u;
+        const bool in = (unsigned)ix < nx && (unsigned)iy < ny && kz < (unsigned)P.nz + 2u;
         float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in) q = __ldg(M.zq + ((int)za + 1) * P.ny * P.nx + (int)ty * P.nx + (int)tx);
+        if (in) q = __ldg(M.zq + ((kz * ny + (unsigned)iy) * nx + (unsigned)ix));
         ra = q.y;
-        rb = zb > za ? q.z : q.y;
-        rc = zc < za ? q.x : q.y;
+        rb = __fadd_rn(fr, P.hz_f) >= 1.0f ? q.z : q.y;
+        rc = fr < P.hz_f ? q.x : q.y;
     } else {
         ra = rb = rc = 0.0f;
     }

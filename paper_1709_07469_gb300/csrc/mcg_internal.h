@@ -34,6 +34,7 @@ struct WalkParams {
     int32_t nx, ny, nz;
     double org[3], sp[3];          // voxel origin / spacing (absolute)
     float org_f[3], inv_sp_f[3];   // origin relative to cen, 1/spacing
+    float hz_f;                    // h / spacing[2]: the copies' z offset in cells
     const float4* zq;              // packed voxel grid (layers iz-1, iz, iz+1 per cell), or null
     // boundary data
     int32_t g_kind;

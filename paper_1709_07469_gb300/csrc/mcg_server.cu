@@ -662,7 +662,7 @@ int mcg_model_create(const mcg_domain* domain, const mcg_density* density, const
     }
     // packed copies for the walk's 16-byte loads (the grid one only while the
     // copies' layers stay within one cell of each other: h <= spacing_z / 2)
-    if (density->kind == MCG_RHO_VOXEL && P.h_f * P.inv_sp_f[2] <= 0.5f) {
+    if (density->kind == MCG_RHO_VOXEL && P.hz_f <= 0.5f) {
         const size_t b = mcg_voxel_pack_bytes(density->nx, density->ny, density->nz);
         if ((e = cudaMalloc(&m->zpack, b))) {
             mcg_model_destroy(m);
