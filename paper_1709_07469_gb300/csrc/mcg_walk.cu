@@ -710,7 +710,11 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             continue;  // the last warp: take over the pooled walks
         }
 
-#pragma unroll 2
+        // two four-step blocks per iteration for the analytic densities; one
+        // for the voxel grid, whose larger step body (prefetched lookups)
+        // otherwise strains the instruction cache
+        constexpr int kBlocksUnrolled = (RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked) ? 1 : 2;
+#pragma unroll (kBlocksUnrolled)
         for (int k = 0; k < 16; ++k) {
             if (busy) {
                 float z[12];
