@@ -548,6 +548,24 @@ MCG_API int mcg_boundary_tables(const mcg_domain* domain, const mcg_density* den
 MCG_API int mcg_field(const mcg_density* density, const double* points_dev, int64_t n, double* phi_dev,
                       double* gz_dev, void* stream);
 
+/* mcg_density_at: the density the walks read (Sec. 2.3 step 3: rho at the
+ * walk's points), sampled at n points and at their common-random-number
+ * copies: out[3 i + 0, 1, 2] = rho at (x, y, z), (x, y, z + h), (x, y, z - h).
+ *   precision MCG_MIXED: the mixed walk's single-precision sampler, the point
+ *     taken relative to the domain centre in single precision as the walk
+ *     starts it (the packed grid when density->zpack is set and h <= half a
+ *     cell, else the plain grid: the same values);
+ *   precision MCG_FP64: the plain walk's double-precision sampler, the copies
+ *     at z + h and z - h rounded in double precision.
+ * Cells are half-open [lo, hi); outside the grid, the prism or the sphere the
+ * density is 0, also for points far outside the domain.  points_dev: DEVICE,
+ * n x 3 (absolute coordinates).  out_dev: DEVICE, 3 n doubles (single-
+ * precision values widened exactly).  Asynchronous on `stream`; allocates
+ * nothing.  MCG_ERR_ARG for a bad domain or density, h < 0, or a null buffer
+ * with n > 0. */
+MCG_API int mcg_density_at(const mcg_domain* domain, const mcg_density* density, double h, int32_t precision,
+                           const double* points_dev, int64_t n, double* out_dev, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Measured peaks (the denominators of the walk's roofline).                */
 /* ---------------------------------------------------------------------- */

@@ -26,8 +26,8 @@
 /* Philox4x32-10 (Salmon et al., "Parallel random numbers: as easy as  */
 /* 1, 2, 3", SC'11): a 10-round Feistel-like bijection of a 128-bit    */
 /* counter under a 64-bit key.  The paper (Sec. 2.3) does not name its */
-/* generator; Philox keyed by (seed, station, path) is this build's    */
-/* reading.  Round: two 32x32->64 products of counter words 0 and 2    */
+/* generator; Philox keyed by (seed, station, path) is the reading     */
+/* taken here.  Round: two 32x32->64 products of counter words 0 and 2 */
 /* with the published multipliers, the high halves xor-ed with the     */
 /* other two words and the round key; the key advances by the          */
 /* published Weyl increments between rounds.                           */

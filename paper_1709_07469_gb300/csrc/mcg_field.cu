@@ -161,6 +161,37 @@ __global__ void __launch_bounds__(kFieldThreads) field_voxel_kernel(const FieldP
     }
 }
 
+// The walks' own density samplers at given points and their two copies
+// (x, y, z + h), (x, y, z - h), out[3 i + c]: the mixed walk's single-
+// precision sampler on the point taken relative to the domain centre (the
+// walk's frame), or the plain walk's double-precision sampler.
+template <int RHO>
+__global__ void density_f32_kernel(const WalkParams P, const double* __restrict__ x, int64_t n,
+                                   double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float wx = (float)(x[3 * i] - P.cen[0]), wy = (float)(x[3 * i + 1] - P.cen[1]),
+                wz = (float)(x[3 * i + 2] - P.cen[2]);
+    float a, b, c;
+    rho3_f32<RHO>(P, model_of(P), wx, wy, wz, P.h_f, a, b, c);
+    out[3 * i] = a;
+    out[3 * i + 1] = b;
+    out[3 * i + 2] = c;
+}
+
+__global__ void density_f64_kernel(const WalkParams P, const double* __restrict__ x, int64_t n,
+                                   double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double off[3] = {0.0, P.h, -P.h};
+    for (int c = 0; c < 3; ++c) {
+        const double X[3] = {x[3 * i], x[3 * i + 1], __dadd_rn(x[3 * i + 2], off[c])};
+        out[3 * i + c] = rho_f64(P, model_of(P), X);
+    }
+}
+
 }  // namespace
 
 void preload_field_kernels()
@@ -168,6 +199,11 @@ void preload_field_kernels()
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, (const void*)field_closed_kernel) != cudaSuccess) cudaGetLastError();
     if (cudaFuncGetAttributes(&a, (const void*)field_voxel_kernel) != cudaSuccess) cudaGetLastError();
+    const void* fns[6] = {(const void*)density_f64_kernel,           (const void*)density_f32_kernel<MCG_RHO_NONE>,
+                          (const void*)density_f32_kernel<MCG_RHO_SPHERE>, (const void*)density_f32_kernel<MCG_RHO_PRISM>,
+                          (const void*)density_f32_kernel<MCG_RHO_VOXEL>,  (const void*)density_f32_kernel<kRhoVoxelPacked>};
+    for (const void* f : fns)
+        if (cudaFuncGetAttributes(&a, f) != cudaSuccess) cudaGetLastError();
 }
 
 }  // namespace mcg
@@ -233,4 +269,46 @@ extern "C" int mcg_field(const mcg_density* density, const double* points_dev, i
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MCG_OK : set_error(MCG_ERR_CUDA, "field kernel launch: %s", cudaGetErrorString(e));
+}
+
+extern "C" int mcg_density_at(const mcg_domain* domain, const mcg_density* density, double h, int32_t precision,
+                              const double* points_dev, int64_t n, double* out_dev, void* stream)
+{
+    if (!domain || !density) return set_error(MCG_ERR_ARG, "null domain or density");
+    if (precision != MCG_FP64 && precision != MCG_MIXED) return set_error(MCG_ERR_ARG, "bad precision");
+    if (!(h >= 0.0) || !std::isfinite(h)) return set_error(MCG_ERR_ARG, "h must be finite and non-negative");
+    if (n < 0) return set_error(MCG_ERR_ARG, "n must be non-negative");
+    mcg_boundary zero;
+    std::memset(&zero, 0, sizeof(zero));
+    zero.kind = MCG_G_ZERO;
+    mcg_options o;
+    mcg_options_default(&o);
+    o.h = h;
+    o.crn_gz = 1;
+    o.precision = precision;
+    WalkParams P;
+    const int rc = make_params(domain, density, &zero, 1.0, 0, &o, P);
+    if (rc) return rc;
+    if (n == 0) return MCG_OK;
+    if (!points_dev || !out_dev) return set_error(MCG_ERR_ARG, "null device buffer");
+    if (n > 2147483647LL * 128LL) return set_error(MCG_ERR_ARG, "too many points");
+    preload_kernels();
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == MCG_FP64) {
+        density_f64_kernel<<<blocks, 128, 0, st>>>(P, points_dev, n, out_dev);
+    } else {
+        const int kind = (P.rho_kind == MCG_RHO_VOXEL && P.zq) ? kRhoVoxelPacked : P.rho_kind;
+        switch (kind) {
+        case MCG_RHO_SPHERE: density_f32_kernel<MCG_RHO_SPHERE><<<blocks, 128, 0, st>>>(P, points_dev, n, out_dev); break;
+        case MCG_RHO_PRISM: density_f32_kernel<MCG_RHO_PRISM><<<blocks, 128, 0, st>>>(P, points_dev, n, out_dev); break;
+        case MCG_RHO_VOXEL: density_f32_kernel<MCG_RHO_VOXEL><<<blocks, 128, 0, st>>>(P, points_dev, n, out_dev); break;
+        case kRhoVoxelPacked:
+            density_f32_kernel<kRhoVoxelPacked><<<blocks, 128, 0, st>>>(P, points_dev, n, out_dev);
+            break;
+        default: density_f32_kernel<MCG_RHO_NONE><<<blocks, 128, 0, st>>>(P, points_dev, n, out_dev); break;
+        }
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MCG_OK : set_error(MCG_ERR_CUDA, "density kernel launch: %s", cudaGetErrorString(e));
 }

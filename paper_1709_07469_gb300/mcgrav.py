@@ -167,6 +167,8 @@ def load(path: str | None = None):
     lib.mcg_issue_probe.restype = C.c_int
     lib.mcg_field.argtypes = [P(mcg_density), vp, i64, vp, vp, vp]
     lib.mcg_field.restype = C.c_int
+    lib.mcg_density_at.argtypes = [P(mcg_domain), P(mcg_density), d, i32, vp, i64, vp, vp]
+    lib.mcg_density_at.restype = C.c_int
     lib.mcg_philox.argtypes = [vp, vp, i64, vp, vp]
     lib.mcg_philox.restype = C.c_int
     lib.mcg_normals.argtypes = [u64, u32, u32, u32, i64, i32, vp, vp]
@@ -384,6 +386,13 @@ def mcg_field(prob: Problem, points_dev, n: int, phi_dev=None, gz_dev=None, stre
     """Exact Phi and dPhi/dz of the problem's density model at n device points."""
     return _check(load().mcg_field(C.byref(prob.density), _ptr(points_dev), n, _ptr(phi_dev), _ptr(gz_dev),
                                    _stream_handle(stream)))
+
+
+def mcg_density_at(prob: Problem, h: float, precision: int, points_dev, n: int, out_dev, stream=None) -> int:
+    """The walks' density sampler at n device points and their copies z +- h
+    (out: 3 n doubles on the device)."""
+    return _check(load().mcg_density_at(C.byref(prob.domain), C.byref(prob.density), h, precision,
+                                        _ptr(points_dev), n, _ptr(out_dev), _stream_handle(stream)))
 
 
 STATE_FIELDS = ("n", "mean_u", "m2_u", "mean_d", "m2_d", "steps")

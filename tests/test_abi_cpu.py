@@ -161,3 +161,14 @@ def test_walk_index_limits_without_gpu(lib):
                           w.dt, 0, C.byref(opts), fake, fake, fake, fake, fake, fake)
         assert rc == M.MCG_ERR_ARG, (p0, N)
         assert ("non-negative" if p0 < 0 else "32 bits") in M.last_error()
+
+
+def test_density_at_checks_arguments_without_gpu(lib):
+    w = W.sphere_line()
+    prob = M.problem(w)
+    for h, prec in ((0.01, 7), (-1.0, M.MCG_MIXED), (float("nan"), M.MCG_FP64)):
+        with pytest.raises(M.McgError):
+            M.mcg_density_at(prob, h, prec, None, 3, None)
+    with pytest.raises(M.McgError):  # n > 0 with null buffers
+        M.mcg_density_at(prob, 0.01, M.MCG_MIXED, None, 3, None)
+    assert M.mcg_density_at(prob, 0.01, M.MCG_MIXED, None, 0, None) == M.MCG_OK
