@@ -55,10 +55,11 @@ FP64_OPS_PER_RNG_STEP = 118.8
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one walk_mixed_kernel launch per work item,
 # from ncu's dram__bytes_read.sum + dram__bytes_write.sum on 30 x 8192 items of
-# this workload (37.2-38.2 MB per launch over three launches);
-# traffic grows with the items, so a launch of n items moves ~153 n bytes.
-# To be re-measured (or reported as null) whenever the walk kernel changes.
-WALK_DRAM_BYTES_PER_ITEM = 153.0
+# this workload (36.1 and 37.7 MB per launch over two launches, taken with the
+# block-level quiet test); traffic grows with the items, so a launch of n
+# items moves ~150 n bytes.  To be re-measured (or reported as null) whenever
+# the walk kernel changes.
+WALK_DRAM_BYTES_PER_ITEM = 150.0
 
 
 def parse():

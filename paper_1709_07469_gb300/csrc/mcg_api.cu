@@ -316,6 +316,11 @@ int make_params(const mcg_domain* D, const mcg_density* R, const mcg_boundary* B
         } else if (R->kind == MCG_RHO_SPHERE) {
             const double rf = R->radius + P.h + margin;
             P.far_r2 = (float)(rf * rf);
+            // the cube around that ball, for tests of a whole step block
+            for (int k = 0; k < 3; ++k) {
+                P.far_c[k] = P.sc_f[k];
+                P.far_h[k] = (float)rf;
+            }
         }
     }
     P.max_steps = o->max_steps;

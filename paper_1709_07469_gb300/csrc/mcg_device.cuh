@@ -126,6 +126,30 @@ __device__ __forceinline__ void normals12_f32(uint32_t s, uint32_t p, uint32_t b
     }
 }
 
+// The same twelve normals in polar form, as the walk consumes them: normal j
+// is nr[j / 2] * cs[j] with cs[j] the cosine (j even) or sine (j odd) of the
+// pair's angle and nr <= 0 the scaled radius with its sign.  Every normal's
+// magnitude is at most -nr[j / 2], which bounds a block's excursion.
+__device__ __forceinline__ void polar_pair_f32(uint32_t w1, uint32_t w2, float lnscale, float& nr, float& c,
+                                               float& sn)
+{
+    nr = -sqrt_approx(lnscale * lg2_approx(u01_f32(w1)));
+    const float a = fmaf(one_plus_mantissa(w2), kTwoPi, kAngleOffset);
+    c = cos_approx(a);
+    sn = sin_approx(a);
+}
+
+__device__ __forceinline__ void polar12_f32(uint32_t s, uint32_t p, uint32_t b, uint32_t k0, uint32_t k1,
+                                            float lnscale, float nr[6], float cs[12])
+{
+#pragma unroll
+    for (uint32_t i = 0; i < 3; ++i) {
+        const uint4 w = philox4x32_10(make_uint4(3u * b + i, p, s, 0u), k0, k1);
+        polar_pair_f32(w.x, w.y, lnscale, nr[2 * i], cs[4 * i], cs[4 * i + 1]);
+        polar_pair_f32(w.z, w.w, lnscale, nr[2 * i + 1], cs[4 * i + 2], cs[4 * i + 3]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The model arrays a walk reads: the launch's own, or (multi-request launch)
 // those of the walk's request.

@@ -539,7 +539,11 @@ __global__ void __launch_bounds__(128) walk_fp64_kernel(const WalkParams P)
 // to 16 blocks (64 steps) between refills, two blocks per loop iteration;
 // after them it flushes the single-precision partial sums into the double
 // sums (a real, warp-uniform branch, so the slow double-precision unit sees
-// one instruction per copy per 64 steps).
+// one instruction per copy per 64 steps).  With a prism or sphere density in
+// the box, a warp whose walks all stay, by the block's radius bound, inside
+// Omega and away from the density for the next four steps only moves them
+// (one test per block instead of one per step); otherwise every step tests
+// the exit and samples the density.
 // ---------------------------------------------------------------------------
 //
 // SEG: a multi-request launch (the segment table maps each item to its
@@ -717,21 +721,45 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
 #pragma unroll (kBlocksUnrolled)
         for (int k = 0; k < 16; ++k) {
             if (busy) {
-                float z[12];
-                // (a single-request launch reads its key straight from the
-                // launch parameters: uniform across the warp)
-                normals12_f32(s, p, blk, SEG ? k0 : P.key0, SEG ? k1 : P.key1, P.lnscale_f, z);
+                // the block's twelve normals in polar form: coordinate j of
+                // the moves is nr[j / 2] cs[j]; (a single-request launch reads
+                // its key straight from the launch parameters: uniform across
+                // the warp)
+                float nr[6], cs[12];
+                polar12_f32(s, p, blk, SEG ? k0 : P.key0, SEG ? k1 : P.key1, P.lnscale_f, nr, cs);
+                // one fused multiply-add per coordinate and step
+                auto mv = [&](float x, int j) -> float { return fmaf(nr[j >> 1], cs[j], x); };
                 // Voxel grid: the block's four positions are known once its
                 // normals are, so all twelve density loads are issued here
                 // and their latency overlaps the steps (same positions, same
                 // summation order: results are unchanged).
                 constexpr bool kPrefetch = RHO == MCG_RHO_VOXEL || RHO == kRhoVoxelPacked;
+                // Quiet block (box domain, prism or sphere density): no
+                // coordinate moves by more than -(nr[0] + ... + nr[5]) over
+                // the block, so if that bound keeps every copy inside the
+                // conservative box and outside the density's support box for
+                // the whole block, the four steps only move.  The decision is
+                // taken for the warp (all live lanes quiet), so a warp never
+                // runs both the quiet moves and the full steps.
+                constexpr bool kBlockTest = !BALL && !kPrefetch &&
+                                            (RHO == MCG_RHO_PRISM || RHO == MCG_RHO_SPHERE);
+                bool all_quiet = false;
+                if constexpr (kBlockTest) {
+                    const float rs = ((nr[0] + nr[1]) + (nr[2] + nr[3])) + (nr[4] + nr[5]);  // <= 0
+                    const bool quiet = fabsf(wx) - rs < P.in_f[0] && fabsf(wy) - rs < P.in_f[1] &&
+                                       fabsf(wz) - rs < P.in_f[2] &&
+                                       (fabsf(wx - P.far_c[0]) + rs > P.far_h[0] ||
+                                        fabsf(wy - P.far_c[1]) + rs > P.far_h[1] ||
+                                        fabsf(wz - P.far_c[2]) + rs > P.far_h[2]);
+                    all_quiet = __all_sync(__activemask(), quiet);
+                }
                 // common step: every copy surely inside Omega and surely
                 // outside the density's support -> nothing to do but move
                 auto common = [&](float nx, float ny, float nz, bool& inside_all, float& qxy) -> bool {
                     qxy = BALL ? nx * nx + ny * ny : 0.0f;
                     inside_all = BALL ? qxy + nz * nz < P.in_r2_f
                                       : fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] && fabsf(nz) < P.in_f[2];
+                    if constexpr (kBlockTest) return false;  // the block test decided: full step
                     bool no_rho = true;
                     if constexpr (RHO == MCG_RHO_PRISM) {
                         no_rho = !(fabsf(nx - P.far_c[0]) <= P.far_h[0] && fabsf(ny - P.far_c[1]) <= P.far_h[1] &&
@@ -749,90 +777,99 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                     float x = wx, y = wy, zz = wz;
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
-                        x = x + z[3 * m];
-                        y = y + z[3 * m + 1];
-                        zz = zz + z[3 * m + 2];
+                        x = mv(x, 3 * m);
+                        y = mv(y, 3 * m + 1);
+                        zz = mv(zz, 3 * m + 2);
                         px[m] = x;
                         py[m] = y;
                         pz[m] = zz;
                         rho3_f32<RHO>(P, SEG ? M : model_of(P), x, y, zz, hf, rv[m][0], rv[m][1], rv[m][2]);
                     }
                 }
+                if (all_quiet) {
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const float nx = kPrefetch ? px[m] : wx + z[3 * m];
-                    const float ny = kPrefetch ? py[m] : wy + z[3 * m + 1];
-                    const float nz = kPrefetch ? pz[m] : wz + z[3 * m + 2];
-                    bool inside_all;
-                    float qxy;
-                    if (!common(nx, ny, nz, inside_all, qxy)) {  // otherwise rho = 0 at every copy: sums unchanged
-                        if (!inside_all) {
-                            unsigned ins;
-                            if (BALL) {
-                                const float za = nz, zb = nz + hf, zc = nz - hf;
-                                ins = (qxy + za * za < P.R2_f) ? 1u : 0u;
-                                if (CRN) {
-                                    ins |= (qxy + zb * zb < P.R2_f) ? 2u : 0u;
-                                    ins |= (qxy + zc * zc < P.R2_f) ? 4u : 0u;
-                                }
-                            } else {
-                                const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
-                                ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
-                                if (CRN) {
-                                    ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
-                                    ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
-                                }
-                            }
-                            const unsigned out = alive & ~ins;
-                            if (out) {  // some copy left Omega on this step
-                                const unsigned long long it = sh_item[t];
-                                if (out & 1u) put_exit(P, 0, it, wx, wy, wz, nx, ny, nz, S0, sh_D[0][t]);
-                                if (CRN && (out & 2u)) put_exit(P, 1, it, wx, wy, wz, nx, ny, nz + hf, S1, sh_D[1][t]);
-                                if (CRN && (out & 4u)) put_exit(P, 2, it, wx, wy, wz, nx, ny, nz - hf, S2, sh_D[2][t]);
-                                sh_steps[t] += nstep_of(blk, m) * (long long)__popc(out);
-                                alive &= ins;
-                            }
-                            if (BRIDGE && alive) {  // within the bridge band of a face
-                                unsigned faces = 0u;
-                                const unsigned bx = bridge_exits_f32(P, alive, wx, wy, wz, nx, ny, nz, hf, s, p, blk, m,
-                                                                     &faces);
-                                if (bx) {
-                                    const unsigned long long it = sh_item[t];
-                                    const float yb[3] = {nx, ny, nz};
-                                    for (int c = 0; c < 3; ++c) {
-                                        if (!(bx & (1u << c))) continue;
-                                        const float off = c == 0 ? 0.0f : (c == 1 ? hf : -hf);
-                                        float y3[3] = {yb[0], yb[1], yb[2] + off};
-                                        const int f = (int)((faces >> (3 * c)) & 7u);
-                                        y3[f >> 1] = (f & 1) ? P.half_f[f >> 1] : -P.half_f[f >> 1];
-                                        const float part = c == 0 ? S0 : (c == 1 ? S1 : S2);
-                                        put_exit(P, c, it, wx, wy, wz, y3[0], y3[1], y3[2], part, sh_D[c][t]);
-                                    }
-                                    sh_steps[t] += nstep_of(blk, m) * (long long)__popc(bx);
-                                    alive &= ~bx;
-                                }
-                            }
-                        }
-                        float ra, rb, rc;
-                        if constexpr (kPrefetch) {
-                            ra = rv[m][0];
-                            rb = rv[m][1];
-                            rc = rv[m][2];
-                        } else {
-                            rho3_f32<RHO>(P, SEG ? M : model_of(P), nx, ny, nz, hf, ra, rb, rc);
-                        }
-                        S0 += ra;
-                        if (CRN) {
-                            S1 += rb;
-                            S2 += rc;
-                        }
+                    for (int m = 0; m < 4; ++m) {
+                        wx = mv(wx, 3 * m);
+                        wy = mv(wy, 3 * m + 1);
+                        wz = mv(wz, 3 * m + 2);
                     }
-                    wx = nx;
-                    wy = ny;
-                    wz = nz;
-                    // no early exit when the last copy leaves: the remaining
-                    // steps of the block write nothing (no live copy), and a
-                    // branch-free four-step body schedules better
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float nx = kPrefetch ? px[m] : mv(wx, 3 * m);
+                        const float ny = kPrefetch ? py[m] : mv(wy, 3 * m + 1);
+                        const float nz = kPrefetch ? pz[m] : mv(wz, 3 * m + 2);
+                        bool inside_all;
+                        float qxy;
+                        if (!common(nx, ny, nz, inside_all, qxy)) {  // otherwise rho = 0 at every copy: sums unchanged
+                            if (!inside_all) {
+                                unsigned ins;
+                                if (BALL) {
+                                    const float za = nz, zb = nz + hf, zc = nz - hf;
+                                    ins = (qxy + za * za < P.R2_f) ? 1u : 0u;
+                                    if (CRN) {
+                                        ins |= (qxy + zb * zb < P.R2_f) ? 2u : 0u;
+                                        ins |= (qxy + zc * zc < P.R2_f) ? 4u : 0u;
+                                    }
+                                } else {
+                                    const bool inxy = fabsf(nx) < hx && fabsf(ny) < hy;
+                                    ins = (inxy && fabsf(nz) < hz) ? 1u : 0u;
+                                    if (CRN) {
+                                        ins |= (inxy && fabsf(nz + hf) < hz) ? 2u : 0u;
+                                        ins |= (inxy && fabsf(nz - hf) < hz) ? 4u : 0u;
+                                    }
+                                }
+                                const unsigned out = alive & ~ins;
+                                if (out) {  // some copy left Omega on this step
+                                    const unsigned long long it = sh_item[t];
+                                    if (out & 1u) put_exit(P, 0, it, wx, wy, wz, nx, ny, nz, S0, sh_D[0][t]);
+                                    if (CRN && (out & 2u)) put_exit(P, 1, it, wx, wy, wz, nx, ny, nz + hf, S1, sh_D[1][t]);
+                                    if (CRN && (out & 4u)) put_exit(P, 2, it, wx, wy, wz, nx, ny, nz - hf, S2, sh_D[2][t]);
+                                    sh_steps[t] += nstep_of(blk, m) * (long long)__popc(out);
+                                    alive &= ins;
+                                }
+                                if (BRIDGE && alive) {  // within the bridge band of a face
+                                    unsigned faces = 0u;
+                                    const unsigned bx = bridge_exits_f32(P, alive, wx, wy, wz, nx, ny, nz, hf, s, p, blk, m,
+                                                                         &faces);
+                                    if (bx) {
+                                        const unsigned long long it = sh_item[t];
+                                        const float yb[3] = {nx, ny, nz};
+                                        for (int c = 0; c < 3; ++c) {
+                                            if (!(bx & (1u << c))) continue;
+                                            const float off = c == 0 ? 0.0f : (c == 1 ? hf : -hf);
+                                            float y3[3] = {yb[0], yb[1], yb[2] + off};
+                                            const int f = (int)((faces >> (3 * c)) & 7u);
+                                            y3[f >> 1] = (f & 1) ? P.half_f[f >> 1] : -P.half_f[f >> 1];
+                                            const float part = c == 0 ? S0 : (c == 1 ? S1 : S2);
+                                            put_exit(P, c, it, wx, wy, wz, y3[0], y3[1], y3[2], part, sh_D[c][t]);
+                                        }
+                                        sh_steps[t] += nstep_of(blk, m) * (long long)__popc(bx);
+                                        alive &= ~bx;
+                                    }
+                                }
+                            }
+                            float ra, rb, rc;
+                            if constexpr (kPrefetch) {
+                                ra = rv[m][0];
+                                rb = rv[m][1];
+                                rc = rv[m][2];
+                            } else {
+                                rho3_f32<RHO>(P, SEG ? M : model_of(P), nx, ny, nz, hf, ra, rb, rc);
+                            }
+                            S0 += ra;
+                            if (CRN) {
+                                S1 += rb;
+                                S2 += rc;
+                            }
+                        }
+                        wx = nx;
+                        wy = ny;
+                        wz = nz;
+                        // no early exit when the last copy leaves: the remaining
+                        // steps of the block write nothing (no live copy), and a
+                        // branch-free four-step body schedules better
+                    }
                 }
                 ++blk;
                 if (!alive) {
