@@ -678,13 +678,13 @@ def serving_block(M, W, args):
     targets = rng.choice([1e-2, 3e-3, 1e-3], n)
     mk = rng.integers(0, 16, n)
     st_idx = [rng.choice(base.n_stations, size=int(s), replace=False) for s in S]
-    def config(batch):
-        return M.server_config(M.options(base, precision=M.MCG_MIXED, migrate=args.migrate), chunk_paths=4096,
-                               min_paths=8192, hbm_budget=16 << 30, streams=args.serve_streams, max_active=64,
-                               max_round_paths=args.max_round_paths, batch=batch)
+    def config(batch, graph):
+        return M.server_config(M.options(base, precision=M.MCG_MIXED, migrate=args.migrate, graph=graph),
+                               chunk_paths=4096, min_paths=8192, hbm_budget=16 << 30, streams=args.serve_streams,
+                               max_active=64, max_round_paths=args.max_round_paths, batch=batch)
 
-    def replay(arrivals, batch=1):
-        sv = M.mcg_server_create(config(batch))
+    def replay(arrivals, batch=1, graph=1):
+        sv = M.mcg_server_create(config(batch, graph))
         reqs = [None] * n
         t_start = time.perf_counter()
         i = 0
@@ -716,6 +716,8 @@ def serving_block(M, W, args):
 
     # every round in a launch of its own, for comparison with the shared launches
     alone = replay(np.zeros(n), batch=0)
+    # shared launches issued on the streams instead of as one graph per batch
+    on_stream = replay(np.zeros(n), graph=0)
     closed = replay(np.zeros(n))
     capacity = n / closed["makespan_s"]
     levels = [("closed (all at t = 0)", None, closed)]
@@ -730,12 +732,15 @@ def serving_block(M, W, args):
     return {"requests": n, "capacity_requests_per_s": capacity,
             "capacity_one_launch_per_round": {"requests_per_s": n / alone["makespan_s"],
                                               "p50_ms": alone["p50_ms"], "p99_ms": alone["p99_ms"]},
+            "capacity_batches_without_graphs": {"requests_per_s": n / on_stream["makespan_s"],
+                                                "p50_ms": on_stream["p50_ms"], "p99_ms": on_stream["p99_ms"]},
             "levels": [dict(load=name, rate_per_s=rate, **r) for name, rate, r in levels],
             "model_setup_s": setup_s,
             "config": {"workload": "voxel_survey x 16 models (seeds 0-15)", "stations_per_request": "U{1..64}",
                        "targets": [1e-2, 3e-3, 1e-3], "chunk_paths": 4096, "streams": args.serve_streams,
                        "max_round_paths": args.max_round_paths, "hbm_budget_gib": 16,
-                       "shared_launches": "rounds of compatible requests share walk launches (batch = 1)"}}
+                       "shared_launches": "rounds of compatible requests share walk launches (batch = 1)",
+                       "graphs": "each batch (walk, reductions, result copies) launched as one CUDA graph"}}
 
 
 def run_serving(args):

@@ -161,7 +161,10 @@ typedef struct {
     int32_t refill_min;      /* a warp refills its lanes once at least this many are
                                 free (1..32, default 1; mcg_autotune picks it)    */
     int32_t graph;           /* mcgrav_solve with several batches: capture the batch
-                                sequence in one CUDA graph and launch it (default 1) */
+                                sequence in one CUDA graph and launch it; a server's
+                                walk options: capture each batch of rounds (walk,
+                                reductions, result copies) and launch it as one graph
+                                (default 1) */
     int32_t migrate;         /* mixed walk: once the work list is used up, warps with
                                 few walks left hand them to warps with free lanes
                                 through a pool in work_dev (default 1).  Results do

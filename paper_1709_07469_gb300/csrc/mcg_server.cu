@@ -142,6 +142,9 @@ struct ServerSlot {
     char* dev = nullptr;            // the batch's per-path buffers, walk scratch, table
     size_t bytes = 0;
     bool busy = false;
+    // instantiated graphs of this slot's batches, by the batch's request count
+    // (the topology: one walk, then per request reduce, finalize, copies)
+    std::map<size_t, cudaGraphExec_t> exec;
 };
 
 struct mcg_server {
@@ -271,6 +274,26 @@ int64_t next_round_paths(const mcg_server* sv, const mcg_request* r)
     return n > 0 ? n : chunk;
 }
 
+// Launches a captured batch through the slot's instantiated graph for that
+// request count: updated in place when the topology matches (the usual case),
+// instantiated afresh otherwise.
+cudaError_t launch_slot_graph(ServerSlot& sl, size_t nreq, cudaGraph_t g, cudaStream_t st)
+{
+    auto it = sl.exec.find(nreq);
+    if (it != sl.exec.end()) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(it->second, g, &info) == cudaSuccess) return cudaGraphLaunch(it->second, st);
+        cudaGetLastError();
+        cudaGraphExecDestroy(it->second);
+        sl.exec.erase(it);
+    }
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) return e;
+    sl.exec[nreq] = ex;
+    return cudaGraphLaunch(ex, st);
+}
+
 // Launches one batch of rounds (each request's round_paths already planned)
 // on slot `k`: one walk over all their items, then per request its reduction,
 // finalize and result copies, then the slot's event.  A batch of one request
@@ -337,34 +360,59 @@ int launch_batch(mcg_server* sv, int k, const std::vector<mcg_request*>& reqs)
         P.status = bstatus;  // what no single request can be blamed for (a lost walk)
         P.seg = (const WalkSeg*)(sl.dev + L.seg);
         P.nseg = (int32_t)reqs.size();
-        if ((e = cudaMemcpyAsync(sl.dev + L.seg, sl.h_seg, reqs.size() * sizeof(WalkSeg), cudaMemcpyHostToDevice, st)))
-            return set_error(MCG_ERR_CUDA, "segment table: %s", cudaGetErrorString(e));
     }
     for (mcg_request* r : reqs)  // the first round waits for the admission copies
         if (r->round == 0 && (e = cudaStreamWaitEvent(st, r->ev, 0)))
             return set_error(MCG_ERR_CUDA, "admission order: %s", cudaGetErrorString(e));
-    if ((e = cudaMemsetAsync(bstatus, 0, sizeof(int32_t), st)) || (e = reset_walk(P, st)) ||
-        (e = launch_walk(P, prec, sv->cfg.walk.block ? sv->cfg.walk.block : 128, st)))
-        return set_error(MCG_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
-    for (size_t i = 0; i < reqs.size(); ++i) {
-        mcg_request* r = reqs[i];
-        const ReqLayout RL = req_layout(r->S);
-        mcg_station_state* states = (mcg_station_state*)(r->dev + RL.states);
-        double* res = (double*)(r->dev + RL.res);
-        if ((e = launch_reduce(P.pp_u + begin[i], P.pp_d + begin[i], P.pp_steps + begin[i], r->S, r->round_paths,
-                               states, st)) ||
-            (e = launch_finalize(states, r->S, res, res + r->S, res + 2 * r->S, res + 3 * r->S,
-                                 (int64_t*)(res + 4 * r->S), (int64_t*)(res + 5 * r->S), st)) ||
-            (e = cudaMemcpyAsync(r->h_res, res, 6 * r->S * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
-            (e = cudaMemcpyAsync(r->h_res + 6 * r->S, r->dev + RL.status, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                 st)))
-            return set_error(MCG_ERR_CUDA, "round reduction: %s", cudaGetErrorString(e));
+    // The batch's work on the slot's stream: segment table, walk, then per
+    // request its reduction, finalize and result copies.  With walk.graph the
+    // sequence is captured and launched as one CUDA graph (the slot keeps one
+    // instantiated graph per request count and updates it in place).
+    auto issue = [&]() -> int {
+        if (P.seg &&
+            (e = cudaMemcpyAsync(sl.dev + L.seg, sl.h_seg, reqs.size() * sizeof(WalkSeg), cudaMemcpyHostToDevice, st)))
+            return set_error(MCG_ERR_CUDA, "segment table: %s", cudaGetErrorString(e));
+        if ((e = cudaMemsetAsync(bstatus, 0, sizeof(int32_t), st)) || (e = reset_walk(P, st)) ||
+            (e = launch_walk(P, prec, sv->cfg.walk.block ? sv->cfg.walk.block : 128, st)))
+            return set_error(MCG_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+        for (size_t i = 0; i < reqs.size(); ++i) {
+            mcg_request* r = reqs[i];
+            const ReqLayout RL = req_layout(r->S);
+            mcg_station_state* states = (mcg_station_state*)(r->dev + RL.states);
+            double* res = (double*)(r->dev + RL.res);
+            if ((e = launch_reduce(P.pp_u + begin[i], P.pp_d + begin[i], P.pp_steps + begin[i], r->S,
+                                   r->round_paths, states, st)) ||
+                (e = launch_finalize(states, r->S, res, res + r->S, res + 2 * r->S, res + 3 * r->S,
+                                     (int64_t*)(res + 4 * r->S), (int64_t*)(res + 5 * r->S), st)) ||
+                (e = cudaMemcpyAsync(r->h_res, res, 6 * r->S * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaMemcpyAsync(r->h_res + 6 * r->S, r->dev + RL.status, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st)))
+                return set_error(MCG_ERR_CUDA, "round reduction: %s", cudaGetErrorString(e));
+        }
+        if ((e = cudaMemcpyAsync(h_bstatus, bstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, st)))
+            return set_error(MCG_ERR_CUDA, "batch status: %s", cudaGetErrorString(e));
+        return MCG_OK;
+    };
+    int rc = MCG_OK;
+    if (sv->cfg.walk.graph) {
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)))
+            return set_error(MCG_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+        rc = issue();
+        cudaGraph_t g = nullptr;
+        cudaError_t ge = cudaStreamEndCapture(st, &g);
+        if (rc == MCG_OK && ge == cudaSuccess) ge = launch_slot_graph(sl, reqs.size(), g, st);
+        if (g) cudaGraphDestroy(g);
+        if (rc == MCG_OK && ge != cudaSuccess) rc = set_error(MCG_ERR_CUDA, "batch graph: %s", cudaGetErrorString(ge));
+    } else {
+        rc = issue();
+    }
+    if (rc != MCG_OK) return rc;
+    if ((e = cudaEventRecord(sl.ev, st)))
+        return set_error(MCG_ERR_CUDA, "batch event: %s", cudaGetErrorString(e));
+    for (mcg_request* r : reqs) {
         r->in_flight = true;
         r->slot = k;
     }
-    if ((e = cudaMemcpyAsync(h_bstatus, bstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaEventRecord(sl.ev, st)))
-        return set_error(MCG_ERR_CUDA, "batch event: %s", cudaGetErrorString(e));
     sl.reqs = reqs;
     sl.busy = true;
     sv->used += sl.bytes;
@@ -790,6 +838,7 @@ int mcg_server_destroy(mcg_server* sv)
     sv->th.join();
     for (ServerSlot& sl : sv->slots) {
         cudaStreamSynchronize(sl.st);
+        for (auto& x : sl.exec) cudaGraphExecDestroy(x.second);
         cudaStreamDestroy(sl.st);
         cudaEventDestroy(sl.ev);
         cudaFreeHost(sl.h_seg);

@@ -156,11 +156,11 @@ def test_submit_validation(models):
         M.mcg_server_destroy(sv)
 
 
-def _run_all(models, reqs, batch, **kw):
+def _run_all(models, reqs, batch, graph=1, **kw):
     """All requests submitted at once; (results in order, (launches, rounds))."""
     sph_w = models["sphere"][0]
-    cfg = M.server_config(M.options(sph_w), chunk_paths=CHUNK, min_paths=2 * CHUNK, max_paths=4 * CHUNK,
-                          batch=batch, **kw)
+    cfg = M.server_config(M.options(sph_w, graph=graph), chunk_paths=CHUNK, min_paths=2 * CHUNK,
+                          max_paths=4 * CHUNK, batch=batch, **kw)
     sv = M.mcg_server_create(cfg)
     out = []
     try:
@@ -196,6 +196,32 @@ def test_shared_launches_equal_separate_launches(models):
     assert launches0 == rounds0
     assert launches < rounds, (launches, rounds)       # rounds did share launches
     for (name, _, _, _), a, b in zip(reqs, shared, alone):
+        for k in ("n_paths", "path_steps"):
+            assert np.array_equal(a[k], b[k]), (name, k)
+        if name.startswith("voxel"):
+            for k in ("u", "gz"):
+                np.testing.assert_allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.abs(b["u"]).max(),
+                                           err_msg=f"{name} {k}")
+        else:
+            for k in ("u", "gz", "se_u", "se_gz"):
+                assert np.array_equal(a[k], b[k]), (name, k)
+
+
+def test_graph_batches_equal_stream_batches(models):
+    """Each batch of rounds (segment table, shared walk, every request's
+    reduction, finalize and result copies) captured and launched as one CUDA
+    graph -- the slot's instantiated graph updated in place from batch to batch
+    -- gives what the same batches issued on the stream give: sphere and prism
+    bit for bit, voxel to the flush rounding, path and step counts equal, and
+    the same number of walk launches for the same rounds."""
+    sw, pw, vw = models["sphere"][0], models["prism"][0], models["voxel"][0]
+    reqs = [("voxel", vw.stations[:5], 1e-9, 41), ("sphere", sw.stations[:4], 5e-3, 42),
+            ("voxel2", vw.stations[60:63], 1e-9, 43), ("prism", pw.stations[3:5], 2e-2, 44),
+            ("sphere", sw.stations[4:6], 1e-2, 45), ("voxel", vw.stations[200:201], 1e-9, 46)]
+    g, (launches_g, rounds_g) = _run_all(models, reqs, 1, graph=1, streams=2)
+    n, (launches_n, rounds_n) = _run_all(models, reqs, 1, graph=0, streams=2)
+    assert rounds_g == rounds_n and launches_g < rounds_g
+    for (name, _, _, _), a, b in zip(reqs, g, n):
         for k in ("n_paths", "path_steps"):
             assert np.array_equal(a[k], b[k]), (name, k)
         if name.startswith("voxel"):
