@@ -330,16 +330,18 @@ MCG_API int mcg_finalize(const mcg_station_state* states_dev, int64_t S, double*
 MCG_API int mcg_states_merge(const mcg_station_state* parts, int64_t R, int64_t S, mcg_station_state* out);
 
 /* mcg_autotune: picks the launch shape of the walk for this problem and
- * writes it into *opts, in two stages timed with CUDA events:
- *   1. opts->block (64, 96, 128) and opts->refill_min (1, 4, 16) on short
- *      walks of the given stations capped at 2048 RNG-steps (the stepping
- *      rate, every lane busy);
- *   2. mixed walk with migrate = 1: opts->spill_max (8, 16, 24, 32) on
- *      uncapped walks, two per resident lane, whose launch ends in the
- *      exit-time tail that walk migration shortens: the median of three
- *      timed launches per value, and the incoming value (24 when unset)
- *      stays unless another is more than 1 % faster (skipped for the FP64
- *      walk; stops early, keeping it, once one launch takes over 2 s).
+ * writes it into *opts, in two stages timed with CUDA events (one warm-up
+ * launch, then the median of three timed launches per candidate):
+ *   1. opts->block (64, 96, 128) on short walks of the given stations capped
+ *      at 2048 RNG-steps (the stepping rate, every lane busy; all walks of a
+ *      warp end together, so the refill policy plays no part);
+ *   2. mixed walk: opts->refill_min (1, 4, 16) x opts->spill_max (8, 16, 24,
+ *      32; with migrate = 1 only) on uncapped walks, two per resident lane,
+ *      whose launch ends in the exit-time tail: lanes free up at random steps
+ *      and walk migration shortens the tail.  The defaults (refill 1, the
+ *      incoming spill threshold, 24 when unset) stay unless another pair is
+ *      more than 1 % faster (skipped for the FP64 walk; stops early, keeping
+ *      them, once one launch takes over 2 s).
  * stations_dev: DEVICE, S x 3.  Blocking; allocates and frees a scratch
  * area of mcg_walk's size for the larger of the two stages. */
 MCG_API int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,

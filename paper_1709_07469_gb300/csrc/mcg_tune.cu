@@ -36,7 +36,7 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
     int64_t N2 = (2 * lanes + S - 1) / S;
     if ((double)N2 * (double)S > 1048576.0) N2 = (1048576 + S - 1) / S;
     if (N2 < 1) N2 = 1;
-    const bool stage2 = o.precision == MCG_MIXED && o.migrate;
+    const bool stage2 = o.precision == MCG_MIXED;
     const int64_t Nmax = (stage2 && N2 > N1) ? N2 : N1;
     const size_t n = (size_t)S * (size_t)Nmax;
     const size_t work = mcg_walk_work_bytes(S, Nmax, o.precision);
@@ -68,69 +68,78 @@ int mcg_autotune(const mcg_domain* domain, const mcg_density* density, const mcg
         cudaEventElapsedTime(&ms, a, b);
         return ms;
     };
+    // median of three timings
+    auto med3 = [](const float* t) {
+        const float a = t[0], b = t[1], c = t[2];
+        return a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
+    };
+    // Stage 1: block size, on capped walks (every walk of a warp ends at the
+    // cap together, so the refill policy plays no part here); one warm-up
+    // launch, then the median of three launches per candidate.
     const int blocks[3] = {64, 96, 128};
-    const int refills[3] = {1, 4, 16};
-    float best = 1e30f;
     int best_block = 128, best_refill = 1, best_spill = P.spill_max;
     rc = MCG_OK;
     P.N = N1;
     P.total = (unsigned long long)S * (unsigned long long)N1;
     if (o.precision == MCG_MIXED) bind_work(P, w, false);
-    for (int rep = 0; rep < 2 && rc == MCG_OK; ++rep) {  // the first pass warms up
+    {
+        float t1[3][3];
+        if (timed(128) < 0.0f) rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+        for (int rep = 0; rep < 3 && rc == MCG_OK; ++rep)
+            for (int bi = 0; bi < 3 && rc == MCG_OK; ++bi) {
+                t1[bi][rep] = timed(blocks[bi]);
+                if (t1[bi][rep] < 0.0f) rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+            }
+        float best = 1e30f;
         for (int bi = 0; bi < 3 && rc == MCG_OK; ++bi)
-            for (int ri = 0; ri < 3 && rc == MCG_OK; ++ri) {
-                P.refill_min = refills[ri];
-                const float ms = timed(blocks[bi]);
-                if (ms < 0.0f) {
-                    rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
-                    break;
-                }
-                if (rep == 1 && ms < best) {
-                    best = ms;
-                    best_block = blocks[bi];
-                    best_refill = refills[ri];
-                }
+            if (med3(t1[bi]) < best) {
+                best = med3(t1[bi]);
+                best_block = blocks[bi];
             }
     }
-    if (rc == MCG_OK && stage2) {
+    // Stage 2 (mixed walk): refill threshold x spill threshold, on uncapped
+    // walks whose launch ends in the exit-time tail (refills happen as walks
+    // exit at random steps, and migration shortens the tail).  One timing per
+    // candidate is noisy there: the median of three decides, and the default
+    // (refill 1, the options' spill threshold) stays unless another pair is
+    // faster by more than 1 %.
+    if (rc == MCG_OK && o.precision == MCG_MIXED) {
         P.max_steps = opts->max_steps;
-        P.refill_min = best_refill;
         P.N = N2;
         P.total = (unsigned long long)S * (unsigned long long)N2;
-        bind_work(P, w, true);
-        // A launch of uncapped walks ends in its longest walks, so one timing
-        // per candidate is noisy: the median of three timed launches (after
-        // one warm-up pass) decides, and the default threshold stays unless
-        // another is faster by more than 1 %.
-        const int spills[4] = {8, 16, 24, 32};
-        const int dflt = P.spill_max;
-        float t[4][3];
-        bool too_long = false;  // very long walks: keep the default
-        for (int rep = 0; rep < 4 && rc == MCG_OK && !too_long; ++rep)
-            for (int si = 0; si < 4 && rc == MCG_OK && !too_long; ++si) {
-                P.spill_max = spills[si];
-                const float ms = timed(best_block);
-                if (ms < 0.0f) {
-                    rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
-                    break;
+        bind_work(P, w, o.migrate != 0);
+        const int refills[3] = {1, 4, 16};
+        const int spills_m[4] = {8, 16, 24, 32};
+        const int dflt_spill = P.spill_max;
+        const int* spills = o.migrate ? spills_m : &dflt_spill;
+        const int ns = o.migrate ? 4 : 1;
+        float t2[3][4][3];
+        P.refill_min = 1;
+        const float warm = timed(best_block);
+        if (warm < 0.0f) rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+        const bool too_long = warm > 2000.0f;  // very long walks: keep the defaults
+        for (int rep = 0; rep < 3 && rc == MCG_OK && !too_long; ++rep)
+            for (int ri = 0; ri < 3 && rc == MCG_OK; ++ri)
+                for (int si = 0; si < ns && rc == MCG_OK; ++si) {
+                    P.refill_min = refills[ri];
+                    P.spill_max = spills[si];
+                    t2[ri][si][rep] = timed(best_block);
+                    if (t2[ri][si][rep] < 0.0f)
+                        rc = set_error(MCG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
                 }
-                if (rep > 0) t[si][rep - 1] = ms;
-                too_long = ms > 2000.0f;
-            }
+        best_spill = dflt_spill;
         if (rc == MCG_OK && !too_long) {
-            float med[4], med_dflt = -1.0f;
-            for (int si = 0; si < 4; ++si) {
-                const float a = t[si][0], b = t[si][1], c = t[si][2];
-                med[si] = a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
-                if (spills[si] == dflt) med_dflt = med[si];
-            }
+            float med_dflt = -1.0f;
+            for (int si = 0; si < ns; ++si)
+                if (spills[si] == dflt_spill) med_dflt = med3(t2[0][si]);
             float best2 = med_dflt > 0.0f ? med_dflt / 1.01f : 1e30f;
-            best_spill = dflt;
-            for (int si = 0; si < 4; ++si)
-                if (med[si] < best2) {
-                    best2 = med[si];
-                    best_spill = spills[si];
-                }
+            for (int ri = 0; ri < 3; ++ri)
+                for (int si = 0; si < ns; ++si)
+                    if (med3(t2[ri][si]) < best2) {
+                        best2 = med3(t2[ri][si]);
+                        best_refill = refills[ri];
+                        best_spill = spills[si];
+                    }
         }
         if (too_long) best_spill = opts->spill_max > 0 ? opts->spill_max : 24;
     }

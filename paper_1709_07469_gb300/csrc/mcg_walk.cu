@@ -22,6 +22,8 @@
 // Launch shape: 128 threads, at least MCG_MIXED_MINB blocks per SM (the
 // register bound that gave the best rate; the grid is sized from the
 // occupancy the compiled kernel actually gets).
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include "mcg_device.cuh"
@@ -743,22 +745,36 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                 // runs both the quiet moves and the full steps.
                 constexpr bool kBlockTest = !BALL && !kPrefetch &&
                                             (RHO == MCG_RHO_PRISM || RHO == MCG_RHO_SPHERE);
-                bool all_quiet = false;
-                if constexpr (kBlockTest) {
+                // The same bound with the domain alone: a warp whose copies all
+                // stay surely inside Omega for the block runs its steps without
+                // exit tests.  (Not for the voxel grid: the second copy of the
+                // step body costs its kernel six registers and a sixth of its
+                // resident warps.)
+                constexpr bool kBlockInside = !BALL && !kPrefetch;
+                bool all_quiet = false, all_inside = false;
+                if constexpr (kBlockTest || kBlockInside) {
                     const float rs = ((nr[0] + nr[1]) + (nr[2] + nr[3])) + (nr[4] + nr[5]);  // <= 0
-                    const bool quiet = fabsf(wx) - rs < P.in_f[0] && fabsf(wy) - rs < P.in_f[1] &&
-                                       fabsf(wz) - rs < P.in_f[2] &&
-                                       (fabsf(wx - P.far_c[0]) + rs > P.far_h[0] ||
-                                        fabsf(wy - P.far_c[1]) + rs > P.far_h[1] ||
-                                        fabsf(wz - P.far_c[2]) + rs > P.far_h[2]);
-                    all_quiet = __all_sync(__activemask(), quiet);
+                    const bool inside =
+                        fabsf(wx) - rs < P.in_f[0] && fabsf(wy) - rs < P.in_f[1] && fabsf(wz) - rs < P.in_f[2];
+                    const unsigned am = __activemask();
+                    if constexpr (kBlockTest) {
+                        const bool far = fabsf(wx - P.far_c[0]) + rs > P.far_h[0] ||
+                                         fabsf(wy - P.far_c[1]) + rs > P.far_h[1] ||
+                                         fabsf(wz - P.far_c[2]) + rs > P.far_h[2];
+                        all_quiet = __all_sync(am, inside && far);
+                    }
+                    if constexpr (kBlockInside) all_inside = __all_sync(am, inside);
                 }
                 // common step: every copy surely inside Omega and surely
                 // outside the density's support -> nothing to do but move
-                auto common = [&](float nx, float ny, float nz, bool& inside_all, float& qxy) -> bool {
+                // (ki: the block test already showed every copy inside)
+                auto common = [&](auto ki, float nx, float ny, float nz, bool& inside_all, float& qxy) -> bool {
                     qxy = BALL ? nx * nx + ny * ny : 0.0f;
-                    inside_all = BALL ? qxy + nz * nz < P.in_r2_f
-                                      : fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] && fabsf(nz) < P.in_f[2];
+                    if constexpr (decltype(ki)::value)
+                        inside_all = true;
+                    else
+                        inside_all = BALL ? qxy + nz * nz < P.in_r2_f
+                                          : fabsf(nx) < P.in_f[0] && fabsf(ny) < P.in_f[1] && fabsf(nz) < P.in_f[2];
                     if constexpr (kBlockTest) return false;  // the block test decided: full step
                     bool no_rho = true;
                     if constexpr (RHO == MCG_RHO_PRISM) {
@@ -794,6 +810,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         wz = mv(wz, 3 * m + 2);
                     }
                 } else {
+                    auto full_steps = [&](auto ki) {
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const float nx = kPrefetch ? px[m] : mv(wx, 3 * m);
@@ -801,7 +818,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         const float nz = kPrefetch ? pz[m] : mv(wz, 3 * m + 2);
                         bool inside_all;
                         float qxy;
-                        if (!common(nx, ny, nz, inside_all, qxy)) {  // otherwise rho = 0 at every copy: sums unchanged
+                        if (!common(ki, nx, ny, nz, inside_all, qxy)) {  // otherwise rho = 0 at every copy: sums unchanged
                             if (!inside_all) {
                                 unsigned ins;
                                 if (BALL) {
@@ -870,6 +887,11 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         // steps of the block write nothing (no live copy), and a
                         // branch-free four-step body schedules better
                     }
+                    };
+                    if (kBlockInside && all_inside)
+                        full_steps(std::true_type{});
+                    else
+                        full_steps(std::false_type{});
                 }
                 ++blk;
                 if (!alive) {
