@@ -54,12 +54,12 @@ OPS_PER_PATH_STEP = OPS_PER_RNG_STEP / 3.0
 FP64_OPS_PER_RNG_STEP = 118.8
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one walk_mixed_kernel launch per work item,
-# from ncu's dram__bytes_read.sum + dram__bytes_write.sum on 30 x 8192 items of
-# this workload (36.1 and 37.7 MB per launch over two launches, taken with the
-# block-level quiet test); traffic grows with the items, so a launch of n
-# items moves ~150 n bytes.  To be re-measured (or reported as null) whenever
-# the walk kernel changes.
-WALK_DRAM_BYTES_PER_ITEM = 150.0
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum (one pass) on a
+# full-size launch of this workload, 30 x 131072 items: 41.2 MB read + 405.9 MB
+# written = 113.7 B per item (the 32-byte exit records stay in L2 in smaller
+# launches, so a smaller case does not scale).  To be re-measured (or reported
+# as null) whenever the walk kernel changes.
+WALK_DRAM_BYTES_PER_ITEM = 113.7
 
 
 def parse():
@@ -361,7 +361,7 @@ def run_ours(args):
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
                            "frac": achieved / peak,
                            "traffic": WALK_DRAM_BYTES_PER_ITEM * S * Bp,
-                           "traffic_source": "ncu dram bytes per item on 30 x 8192 items, scaled to the launch",
+                           "traffic_source": "ncu dram bytes of a full-size launch (30 x 131072 items), per item x the launch's items",
                            "kernel": "walk_mixed_kernel<PRISM,crn>",
                            "ops_per_rng_step": OPS_PER_RNG_STEP,
                            "launch_time": "timed region / K (two-stream pipeline)",

@@ -259,8 +259,10 @@ MCG_API int mcgrav_solve(const mcg_domain* domain, const mcg_density* density, c
  * Items that do not finish (cancelled, never started, capped, lost after a
  * timeout, station outside Omega) read pp_u = pp_d = NaN; pp_steps is 0 for
  * items never started.  The call marks every item "no result" before the
- * launch (a stream-ordered fill of 8 B per item, plus 24 B of exit records
- * per item for the mixed walk), so nothing is read from an earlier launch.
+ * launch (a stream-ordered fill of the 8-byte step counts; the mixed walk
+ * flags an item's count once all its copies have written their exit records,
+ * and its exit kernel evaluates flagged items only), so nothing is read from
+ * an earlier launch.
  * Allocates nothing. */
 MCG_API int mcg_walk(const mcg_domain* domain, const mcg_density* density, const mcg_boundary* boundary,
              const double* stations_dev, int64_t S, int64_t p0, int64_t N, double dt, uint64_t seed,
@@ -281,14 +283,15 @@ MCG_API size_t mcg_walk_work_bytes(int64_t S, int64_t N, int32_t precision);
  * work counter and the mixed walk's exit records -- in one fixed device
  * array inside the library (64 MiB, held by every GPU that loads the library
  * until the process exits).  It allocates nothing.
- *   - S * N may not exceed mcg_walk_static_max_items() (about 5.6e5 paths);
+ *   - S * N may not exceed mcg_walk_static_max_items() (about 7.0e5 paths);
  *     larger requests return MCG_ERR_ARG with a message saying so.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
  *   - All calls share the one array and it keeps the last call's contents;
- *     the call zeroes the counter and marks its exit records "no result"
- *     itself, so items that do not finish read NaN as with mcg_walk.  Calls
+ *     the call zeroes the counter and the caller's step counts (the
+ *     completion flags) itself, so items that do not finish read NaN as
+ *     with mcg_walk.  Calls
  *     that overlap on the GPU (other streams, other threads) race on it:
  *     serialise them.
  *   - The array's address is cached per device after the first call; a

@@ -94,9 +94,7 @@ WorkLayout work_layout(size_t n)
     L.cap = n < kPoolMaxSlots ? (unsigned long long)n : kPoolMaxSlots;
     size_t o = 0;
     L.frec = o;
-    o += align256(n * 3 * 8 * sizeof(float));
-    L.drec = o;
-    o += align256(n * 3 * sizeof(double));
+    o += align256(n * 3 * kExitRecordBytes);
     L.pool = o;
     o += align256((size_t)L.cap * kPoolEntryBytes);
     L.ready = o;
@@ -112,7 +110,6 @@ void bind_work(WalkParams& P, void* work, bool migrate)
     const WorkLayout L = work_layout((size_t)P.total);
     unsigned char* w = (unsigned char*)work;
     P.frec = (float*)(w + L.frec);
-    P.drec = (double*)(w + L.drec);
     if (migrate && L.cap > 0) {
         P.pool = w + L.pool;
         P.pool_ready = (uint32_t*)(w + L.ready);
@@ -131,12 +128,12 @@ cudaError_t reset_walk(const WalkParams& P, cudaStream_t st)
     const size_t T = (size_t)P.total;
     cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), st);
     // Items that never finish (cancel, a lost walk) must not read an earlier
-    // launch's values: steps 0, and "no record" for every copy (mixed walk) or
-    // NaN per-path values (FP64 walk, which writes them directly).
+    // launch's values: steps 0, which also clears the mixed walk's completion
+    // flags (its exit kernel writes NaN for items without one), or NaN
+    // per-path values (FP64 walk, which writes them directly).
     if (e == cudaSuccess) e = cudaMemsetAsync(P.pp_steps, 0, T * sizeof(int64_t), st);
-    if (e == cudaSuccess && P.drec) e = cudaMemsetAsync(P.drec, 0xFF, 3 * T * sizeof(double), st);
-    if (e == cudaSuccess && !P.drec) e = cudaMemsetAsync(P.pp_u, 0xFF, T * sizeof(double), st);
-    if (e == cudaSuccess && !P.drec) e = cudaMemsetAsync(P.pp_d, 0xFF, T * sizeof(double), st);
+    if (e == cudaSuccess && !P.frec) e = cudaMemsetAsync(P.pp_u, 0xFF, T * sizeof(double), st);
+    if (e == cudaSuccess && !P.frec) e = cudaMemsetAsync(P.pp_d, 0xFF, T * sizeof(double), st);
     if (e == cudaSuccess && P.pool) {
         // flags and counters are adjacent: one memset covers both
         const size_t bytes = (size_t)((unsigned char*)P.pool_ctr - (unsigned char*)P.pool_ready) + 256;
@@ -409,8 +406,8 @@ int static_scratch(int dev, unsigned char** base)
 int64_t static_max_items()
 {
     const size_t avail = (size_t)MCG_STATIC_SCRATCH_BYTES - 256;
-    int64_t n = (int64_t)((avail - 512) / (3 * 8 * sizeof(float) + 3 * sizeof(double)));
-    while (n > 0 && align256((size_t)n * 3 * 8 * sizeof(float)) + align256((size_t)n * 3 * sizeof(double)) > avail) --n;
+    int64_t n = (int64_t)(avail / (3 * kExitRecordBytes));
+    while (n > 0 && align256((size_t)n * 3 * kExitRecordBytes) > avail) --n;
     return n;
 }
 
@@ -856,12 +853,12 @@ int mcg_walk_static(const mcg_domain* domain, const mcg_density* density, const 
     P.counter = (unsigned long long*)base;
     if (opts->precision == MCG_MIXED) {
         P.frec = (float*)(base + 256);
-        P.drec = (double*)(base + 256 + align256(n * 3 * 8 * sizeof(float)));
     }
     cudaStream_t st = (cudaStream_t)opts->stream;
-    // the counter starts at zero and every item at "no result", so that an
-    // item that does not finish (cancel) never reads the last call's records
-    // left in the shared array; there is no migration pool here
+    // the counter starts at zero and every item without its completion flag
+    // (the step counts are cleared), so that an item that does not finish
+    // (cancel) never reads the last call's records left in the shared array;
+    // there is no migration pool here
     e = reset_walk(P, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(static scratch)");
     e = launch_walk(P, opts->precision, opts->block ? opts->block : 128, st);

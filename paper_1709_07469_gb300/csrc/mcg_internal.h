@@ -60,8 +60,7 @@ struct WalkParams {
     int64_t* pp_steps;
     int32_t* status;
     unsigned long long* counter;
-    float* frec;                   // mixed walk: exit records (8 floats per copy per item)
-    double* drec;                  // mixed walk: flushed sums per copy per item
+    float* frec;                   // mixed walk: exit records (32 bytes per copy per item), or null
     volatile int32_t* cancel;
     // mixed walk, migration of walks between warps once the work list is used
     // up (null pool: off).  pool: kPoolEntryBytes per slot; pool_ready: one
@@ -95,10 +94,12 @@ struct WalkSeg {
     uint32_t key0, key1;
 };
 
-// Exit-record marker of an item without a result (never started, cancelled,
-// capped, lost, station outside Omega): the all-ones double, a NaN pattern
-// that no floating-point operation produces, written by a byte fill.
-constexpr long long kNoRecordBits = -1LL;
+// Completion flag of a mixed-walk item, kept in its step count: set when every
+// copy has left Omega and written its exit record.  The exit kernel evaluates
+// flagged items only and clears the flag; an item without it (never started,
+// cancelled, capped, lost, station outside Omega) gets NaN.  Step counts stay
+// far below 2^62.
+constexpr long long kDoneFlag = 1LL << 62;
 
 // Kernel-template tag of the voxel density read through the packed grid
 // (WalkParams::zq); not a public density kind.
@@ -108,9 +109,10 @@ constexpr size_t kPoolEntryBytes = 80;
 constexpr unsigned long long kPoolMaxSlots = 1ull << 19;
 
 // Offsets inside the mixed walk's scratch of n = S * N items (mcg_api.cu):
-// exit records, flushed sums, migration pool, ready flags, pool counters.
+// exit records, migration pool, ready flags, pool counters.
+constexpr size_t kExitRecordBytes = 32;
 struct WorkLayout {
-    size_t frec, drec, pool, ready, ctr, total;
+    size_t frec, pool, ready, ctr, total;
     unsigned long long cap;
 };
 WorkLayout work_layout(size_t n);

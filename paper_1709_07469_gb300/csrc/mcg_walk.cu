@@ -40,8 +40,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kNaN = __builtin_nan("");
 
-__device__ __forceinline__ double no_record() { return __longlong_as_double(kNoRecordBits); }
-__device__ __forceinline__ bool has_record(double d) { return __double_as_longlong(d) != kNoRecordBits; }
 
 // Claims new items for the lanes of this warp that are free.  Returns the
 // claimed item in `item`; lanes beyond the end of the work list become
@@ -83,8 +81,7 @@ __device__ __forceinline__ bool station_ok(const WalkParams& P, const double* st
     if (!ok) {
         P.pp_u[item] = kNaN;
         P.pp_d[item] = kNaN;
-        P.pp_steps[item] = 0;
-        if (P.drec) P.drec[item] = no_record();  // the exit kernel then writes NaN too
+        P.pp_steps[item] = 0;  // no completion flag: the mixed walk's exit kernel writes NaN too
         atomicOr(status, 1 << MCG_ERR_ARG);
     }
     return ok;
@@ -257,13 +254,12 @@ __device__ __noinline__ double exit_fp64(const WalkParams& P, const ModelRef& M,
 
 // Mixed walk exit (run by exit_mixed_kernel, one thread per path, so the
 // double-precision work is convergent): X, Y relative to the box centre in
-// single precision as the walk computed them; the flushed + partial sums give
-// S = rho_0 / 2 + sum_{n=1}^{N-1} rho_n, so the trapezoid integral over the
-// inside steps is dt (S - rho_{N-1} / 2).
+// single precision as the walk computed them; the walk's sum acc (flushed +
+// partial) is S = rho_0 / 2 + sum_{n=1}^{N-1} rho_n, so the trapezoid integral
+// over the inside steps is dt (S - rho_{N-1} / 2).
 __device__ __forceinline__ double exit_mixed(const WalkParams& P, const ModelRef& M, const float* Xf, const float* Yf,
-                                             double flushed, float partial, float rp)
+                                             double acc, float rp)
 {
-    const double acc = flushed + (double)partial;
     double X[3], dW[3], xs[3];
     for (int k = 0; k < 3; ++k) {
         X[k] = (double)Xf[k];
@@ -301,25 +297,21 @@ __device__ __forceinline__ double exit_mixed(const WalkParams& P, const ModelRef
     return boundary_value<true>(P, M, face, xs) - P.two_pi_G * I;
 }
 
-// Exit records of the mixed walk (structure of arrays, item-major):
-//   frec[(8 c + f) * total + item], f = 0..2 walk position X before the exit
-//        step (copy 0's coordinates; copy c adds its z offset), 3..5 Y, 6 partial sum
-//   drec[c * total + item]          flushed double sum (NaN: no result)
-// rho at X is not stored: exit_mixed_kernel evaluates the same single-precision
-// density function at the same X, which gives the walk's value bit for bit.
+// Exit record of copy c of item `item` (record c * total + item of frec):
+// 32 bytes, written as two 16-byte stores that fill one sector -- X (the walk
+// position before the exit step, copy 0's coordinates; copy c adds its z
+// offset), Y (the copy's first point not strictly inside Omega) and the
+// source sum flushed + partial in double.  rho at X is not stored:
+// exit_mixed_kernel evaluates the same single-precision density function at
+// the same X, which gives the walk's value bit for bit.  The record is valid
+// once the item's step count carries kDoneFlag.
 __device__ __forceinline__ void put_exit(const WalkParams& P, int c, unsigned long long item, float x0, float x1,
                                          float x2, float y0, float y1, float y2, float partial, double flushed)
 {
-    float* f = P.frec + (size_t)8 * c * P.total + item;
-    const size_t T = P.total;
-    f[0] = x0;
-    f[T] = x1;
-    f[2 * T] = x2;
-    f[3 * T] = y0;
-    f[4 * T] = y1;
-    f[5 * T] = y2;
-    f[6 * T] = partial;
-    P.drec[(size_t)c * T + item] = flushed;
+    const double acc = flushed + (double)partial;
+    float4* r = (float4*)P.frec + 2 * ((size_t)c * P.total + item);
+    r[0] = make_float4(x0, x1, x2, y0);
+    r[1] = make_float4(y1, y2, __int_as_float(__double2loint(acc)), __int_as_float(__double2hiint(acc)));
 }
 
 __device__ __forceinline__ void write_path(const WalkParams& P, int32_t* status, unsigned long long item, double u0,
@@ -595,8 +587,7 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
             // walks in flight, pooled walks and unclaimed items give no result
             if (lane == 0) atomicOr(P.status, 1 << MCG_ERR_CANCELLED);
             if (busy) {
-                const unsigned long long it = sh_item[t];
-                P.drec[it] = no_record();
+                const unsigned long long it = sh_item[t];  // (no completion flag: NaN)
                 P.pp_steps[it] = sh_steps[t] + (long long)__popc(alive) * 4 * (long long)blk;
             }
             busy = false;
@@ -894,13 +885,13 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                         full_steps(std::false_type{});
                 }
                 ++blk;
-                if (!alive) {
-                    P.pp_steps[sh_item[t]] = sh_steps[t];
+                if (!alive) {  // every copy has its exit record: mark the item complete
+                    P.pp_steps[sh_item[t]] = sh_steps[t] | kDoneFlag;
                     busy = false;
                 } else if (4 * (int64_t)blk >= P.max_steps) {
                     const unsigned long long it = sh_item[t];
                     atomicOr(SEG ? P.seg[sh_seg[t]].status : P.status, 1 << MCG_ERR_STEP_CAP);
-                    P.drec[it] = no_record();  // copy 0 record marks "no result"
+                    // (no completion flag: the exit kernel writes NaN)
                     P.pp_steps[it] = sh_steps[t] + (long long)__popc(alive) * 4 * (long long)blk;
                     busy = false;
                 }
@@ -936,13 +927,14 @@ __device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long lon
     const int nc = P.crn ? 3 : 1;
     const size_t T = P.total;
     for (int c = 0; c < nc; ++c) {
-        const float* f = P.frec + (size_t)8 * c * T + item;
-        const float xb = f[0], yb = f[T], zb = f[2 * T];
+        const float4* rec = (const float4*)P.frec + 2 * ((size_t)c * T + item);
+        const float4 a = rec[0], b = rec[1];
         float r[3];
-        rho3_f32<RHO>(P, M, xb, yb, zb, hf, r[0], r[1], r[2]);
-        const float X[3] = {xb, yb, c == 0 ? zb : (c == 1 ? zb + hf : zb - hf)};
-        const float Y[3] = {f[3 * T], f[4 * T], f[5 * T]};
-        u[c] = exit_mixed(P, M, X, Y, P.drec[(size_t)c * T + item], f[6 * T], r[c]);
+        rho3_f32<RHO>(P, M, a.x, a.y, a.z, hf, r[0], r[1], r[2]);
+        const float X[3] = {a.x, a.y, c == 0 ? a.z : (c == 1 ? a.z + hf : a.z - hf)};
+        const float Y[3] = {a.w, b.x, b.y};
+        const double acc = __hiloint2double(__float_as_int(b.w), __float_as_int(b.z));
+        u[c] = exit_mixed(P, M, X, Y, acc, r[c]);
     }
     const double d = P.crn ? (u[1] - u[2]) / (2.0 * P.h) : kNaN;
     P.pp_u[item] = u[0];
@@ -951,8 +943,9 @@ __device__ __forceinline__ void exit_item(const WalkParams& P, unsigned long lon
 }
 
 // Exit evaluation, convergent: each warp scans its items 32 at a time, writes
-// NaN for the ones without a result (a copy without an exit record: capped,
-// cancelled, never started, lost, outside Omega) and queues the others in
+// NaN for the ones without a result (no completion flag: capped, cancelled,
+// never started, lost, outside Omega), clears the flag of the others and
+// queues them in
 // shared memory, evaluating them 32 at a time, so the slow double-precision
 // pipe never runs a warp whose lanes are mostly idle.
 template <int RHO, bool SEG>
@@ -968,9 +961,9 @@ __global__ void __launch_bounds__(128) exit_mixed_kernel(const WalkParams P)
     for (unsigned long long base = first; base < P.total; base += warps * 32ull) {
         const unsigned long long item = base + (unsigned long long)lane;
         const bool in = item < P.total;
-        bool valid = in && has_record(P.drec[item]);
-        if (P.crn && valid)
-            valid = has_record(P.drec[P.total + item]) && has_record(P.drec[2 * P.total + item]);
+        const long long steps = in ? (long long)P.pp_steps[item] : 0ll;
+        const bool valid = (steps & kDoneFlag) != 0;
+        if (valid) P.pp_steps[item] = steps & ~kDoneFlag;
         if (in && !valid) {
             P.pp_u[item] = kNaN;
             P.pp_d[item] = kNaN;
