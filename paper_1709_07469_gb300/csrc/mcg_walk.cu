@@ -857,18 +857,31 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                                     }
                                 }
                             }
-                            float ra, rb, rc;
-                            if constexpr (kPrefetch) {
-                                ra = rv[m][0];
-                                rb = rv[m][1];
-                                rc = rv[m][2];
+                            if constexpr (RHO == MCG_RHO_PRISM) {
+                                // the prism's density is rho0 or 0: add rho0 where a
+                                // copy is inside (the tests of rho3_f32<PRISM>)
+                                const bool inxy = nx >= P.plo_f[0] && nx < P.phi_f[0] && ny >= P.plo_f[1] &&
+                                                  ny < P.phi_f[1];
+                                const float zb = __fadd_rn(nz, hf), zc = __fsub_rn(nz, hf);
+                                if (inxy && nz >= P.plo_f[2] && nz < P.phi_f[2]) S0 += P.rho0_f;
+                                if (CRN) {
+                                    if (inxy && zb >= P.plo_f[2] && zb < P.phi_f[2]) S1 += P.rho0_f;
+                                    if (inxy && zc >= P.plo_f[2] && zc < P.phi_f[2]) S2 += P.rho0_f;
+                                }
                             } else {
-                                rho3_f32<RHO>(P, SEG ? M : model_of(P), nx, ny, nz, hf, ra, rb, rc);
-                            }
-                            S0 += ra;
-                            if (CRN) {
-                                S1 += rb;
-                                S2 += rc;
+                                float ra, rb, rc;
+                                if constexpr (kPrefetch) {
+                                    ra = rv[m][0];
+                                    rb = rv[m][1];
+                                    rc = rv[m][2];
+                                } else {
+                                    rho3_f32<RHO>(P, SEG ? M : model_of(P), nx, ny, nz, hf, ra, rb, rc);
+                                }
+                                S0 += ra;
+                                if (CRN) {
+                                    S1 += rb;
+                                    S2 += rc;
+                                }
                             }
                         }
                         wx = nx;
