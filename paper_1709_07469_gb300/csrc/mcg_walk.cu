@@ -731,7 +731,9 @@ __global__ void __launch_bounds__(128, MCG_MIXED_MINB) walk_mixed_kernel(const W
                 // coordinate moves by more than -(nr[0] + ... + nr[5]) over
                 // the block, so if that bound keeps every copy inside the
                 // conservative box and outside the density's support box for
-                // the whole block, the four steps only move.  The decision is
+                // the whole block, the four steps only move (the boxes' margin,
+                // 1e-5 of the domain, is some twenty times the single-precision
+                // rounding of the bound and of the four moves).  The decision is
                 // taken for the warp (all live lanes quiet), so a warp never
                 // runs both the quiet moves and the full steps.
                 constexpr bool kBlockTest = !BALL && !kPrefetch &&
